@@ -1,0 +1,332 @@
+#!/usr/bin/env python
+"""Benchmark of the forward delay-and-sum pass (paper Sec. 2, Eq. 2).
+
+Workload (default): 128^3 voxels x 1024 elements x 16 diverging-wave
+transmits, complex IQ channel data with 2048 samples, 20 frames per step
+(seeded speckle + point phantom), float32 storage and sums.  A step is one
+das_forward call on the 20 frames: relayout of the channel data plus the DAS
+kernel.  The inputs (5.4 GB) are larger than L2, so no flush is needed.
+
+Prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead,
+on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "volumes/s, forward DAS at 128^3 voxels x 1024 elements x 16 transmits (IQ, float32)"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--frames", type=int, default=20)
+    ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha1()
+    for f in ("das_tile.cuh", "das_tile_f32.cu", "das_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2606_13259_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def profiled_traffic(storage: str):
+    """DRAM bytes per launch of the tile kernel from the committed ncu summary,
+    if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", f"tile_kernel_paper_iq_{storage}.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"kernel_source_sha1:\s*([0-9a-f]+)", text)
+    t = re.search(r"traffic_bytes_per_launch_full:\s*([0-9.eE+]+)", text)
+    if not m or not t or m.group(1) != kernel_source_hash():
+        return None
+    return float(t.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_inputs(frames: int, rank: int, device):
+    from paper_2606_13259_gb300 import synth as S
+
+    sc = S.scene_paper()
+    y = S.frames(sc, frames, seed=2 + 1000 * rank, n_speckle=20000, points=S.paper_points(sc), device=device)
+    return sc, y
+
+
+def cpu_baseline(sc, y_cpu, frames: int, target_s: float):
+    """The FP64 oracle, as it stands, on a bounded voxel sample of the workload."""
+    import numpy as np
+
+    from oracle import oracle as O
+
+    O.build()
+    rng = np.random.default_rng(123)
+    probe = rng.choice(sc.N, 32, replace=False)
+    t0 = time.perf_counter()
+    O.forward(sc, y_cpu, voxels=probe)
+    dt = time.perf_counter() - t0
+    n = int(max(32, min(sc.N, 32 * target_s / max(dt, 1e-6))))
+    vox = rng.choice(sc.N, n, replace=False)
+    t0 = time.perf_counter()
+    O.forward(sc, y_cpu, voxels=vox)
+    dt = time.perf_counter() - t0
+    volumes = frames * n / sc.N
+    return {"value": volumes / dt, "unit": "volumes/s", "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"{n} random voxels x {frames} frames of the workload ({n / sc.N:.2%} of each volume), "
+                      f"{dt:.1f} s, float64, OpenMP over voxels"}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle timed on the host cores."""
+    import numpy as np
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    sc, y = make_inputs(args.frames, 0, dev)
+    y_cpu = y.cpu().numpy()
+    del y
+    from oracle import oracle as O
+
+    O.build()
+    rng = np.random.default_rng(7)
+    probe = rng.choice(sc.N, 16, replace=False)
+    t0 = time.perf_counter()
+    O.forward(sc, y_cpu, voxels=probe)
+    per_voxel = (time.perf_counter() - t0) / 16
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    n = int(max(16, min(sc.N, budget / max(per_voxel, 1e-9))))
+    for _ in range(args.warmup):
+        O.forward(sc, y_cpu, voxels=rng.choice(sc.N, n, replace=False))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.forward(sc, y_cpu, voxels=rng.choice(sc.N, n, replace=False))
+    dt = (time.perf_counter() - t0) / args.steps
+    value = args.frames * n / sc.N / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "volumes/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": sc.name, "frames_per_step": args.frames, "voxels": sc.N, "elements": sc.M,
+                   "transmits": sc.Q, "samples": sc.K, "sample_per_step_voxels": n},
+        "cpu_baseline": {"value": value, "unit": "volumes/s", "cores": O.num_threads(), "kind": "oracle",
+                         "sample": f"{n} random voxels x {args.frames} frames per step"},
+        "e2e": {"value": value, "unit": "volumes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+
+    from paper_2606_13259_gb300 import Plan
+    from paper_2606_13259_gb300 import build as B
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+
+        dist = dist_mod
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    if rank == 0:
+        B.build()
+    if dist:
+        dist.barrier()
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    sc, y = make_inputs(args.frames, rank, dev)
+    F = args.frames
+    plan = Plan.from_scene(sc, storage=args.storage, max_batch=F)
+    out = torch.empty((F,) + plan.shape, dtype=torch.complex64, device=dev)
+    active = plan.count_active()
+
+    for _ in range(args.warmup):
+        plan.forward(y, out)
+    torch.cuda.synchronize()
+    plan.enable_timing(args.steps)
+    launches0 = plan.info()["kernel_launches"]
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(args.steps):
+        plan.forward(y, out)
+    e1.record(s)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    ms = e0.elapsed_time(e1) / args.steps
+    kern_ms_total, kern_n = plan.timing()
+    kern_ms = kern_ms_total / max(kern_n, 1)
+    launches = plan.info()["kernel_launches"] - launches0
+    if dist:
+        t = torch.tensor([ms, kern_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, kern_ms = float(t[0]), float(t[1])
+
+    # end to end through the C-ABI with host buffers (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        y_host = torch.empty(y.shape, dtype=y.dtype, pin_memory=True)
+        y_host.copy_(y)
+        x_host = torch.empty(out.shape, dtype=out.dtype, pin_memory=True)
+        plan.forward_host(y_host, x_host)
+        n_e2e = max(1, min(args.steps, 5))
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            plan.forward_host(y_host, x_host)
+        dt = (time.perf_counter() - t0) / n_e2e
+        if dist:
+            t = torch.tensor([dt], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t[0])
+        e2e = {"value": world * F / dt, "unit": "volumes/s", "h2d_bytes_per_step": y_host.numel() * 8,
+               "d2h_bytes_per_step": x_host.numel() * 8, "ms_per_step": dt * 1e3}
+        del y_host, x_host
+
+    peaks, peak_src = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    flops = active * F * 16.0          # 8 FMA per contributing (voxel, element, transmit, frame) term
+    achieved = flops / (kern_ms * 1e-3) / 1e12
+    bytes_store = {"f32": 8, "f16": 4, "bf16": 4}[args.storage]
+    alg_bytes = sc.Q * sc.M * sc.K * F * bytes_store + F * sc.N * 8
+    roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp32_peak, "traffic": profiled_traffic(args.storage),
+            "kernel": "tile_kernel (forward DAS)", "kernel_ms": kern_ms,
+            "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz ({peak_src} max SM clock)",
+            "hbm_algorithmic_gbs": alg_bytes / (kern_ms * 1e-3) / 1e9,
+            "hbm_peak_gbs": float(peaks.get("hbm_gbs", 6800.0)),
+            "work_per_launch": f"{active} contributing terms x {F} frames x 16 flop"}
+
+    line = {
+        "metric": METRIC, "value": world * F / (ms * 1e-3), "unit": "volumes/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.storage == "f32" else args.storage,
+        "data": "synthetic (seeded speckle + 10 point targets, time-domain simulator)",
+        "config": {"workload": sc.name, "frames_per_step": F, "voxels": sc.N, "elements": sc.M,
+                   "transmits": sc.Q, "samples": sc.K, "storage": args.storage,
+                   "l2": "inputs 5.4 GB > 129 MB L2, no flush", "per_rank_frames": F},
+        "accumulations_per_s": world * F * sc.N * sc.M * sc.Q / (ms * 1e-3),
+        "contributing_terms_per_volume": active,
+        "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(sc, y.cpu().numpy(), F, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,198 @@
+/*
+ * das.h -- C-ABI of the GB300 volumetric delay-and-sum (DAS) library.
+ *
+ * The library evaluates, on one GPU, the delay-and-sum image of the paper's
+ * Sec. 2 ("Delay-and-sum"):
+ *
+ *   Eq. 1   tau_qmn = tau^tx_qn + ||p_n - r_m|| / c
+ *   Eq. 2   x_bn    = sum_q sum_m w^tx_qn w^rx_mn y_bqm[tau_qmn] e^{+i 2 pi f_d tau_qmn}
+ *
+ * with y[tau] the linear interpolation between the samples k = floor(tau fs)
+ * and k + 1 (Sec. 2, after Eq. 2), the batched channel tensor
+ * y in C^{B x Q x M x K} with samples contiguous (Sec. 2, batched layout),
+ * delays and receive weights computed in-kernel and never stored (Sec. 2,
+ * problem scale; Sec. 3.1).  It also provides the adjoint map (image to
+ * channel data) and the derivative with respect to the speed of sound c.
+ *
+ * Conventions (the paper leaves them open; the library fixes them so):
+ *   - sample k is taken at t = k / fs (0-based);
+ *   - diverging wave from virtual source v: tau^tx = (||p - v|| - ||v - o||) / c,
+ *     t = 0 when the wave passes the reference point o (geometry.t0_ref);
+ *     with options.t0_offset = 0: tau^tx = ||p - v|| / c;
+ *   - plane wave with unit propagation direction d: tau^tx = d . (p - o) / c;
+ *   - no transmit (photoacoustic, Sec. 2): tau^tx = 0;
+ *   - IQ data: the focused sample is y[tau] e^{+i 2 pi f_d tau};
+ *   - receive weight: with e = p - r_m, z = e . n_m, rho = |e x n_m|:
+ *     1 if f_number <= 0, else 1 when z > 0 and rho^2 <= (1 + 1e-6) (z / 2F)^2,
+ *     otherwise 0 (rectangular f-number aperture);
+ *   - a term contributes only when 0 <= k <= K - 2.
+ *
+ * Memory: all "_dev" pointers are device pointers owned by the caller; "_host"
+ * pointers are host memory owned by the caller.  The plan owns its own device
+ * buffers (geometry, per-tile reference delays, channel-data relayout scratch)
+ * and allocates them only in das_plan_create, das_plan_set_tuning (when a
+ * tuning needs more scratch) and the first das_forward_host call; the other
+ * compute calls allocate nothing.  Calls are asynchronous on the given stream unless
+ * stated otherwise; a plan must not be used by two streams at once.
+ *
+ * Errors: every function returns DAS_OK (0) or a DAS_ERR_* code.  Invalid
+ * arguments are rejected before any launch.  das_last_error() returns a
+ * thread-local text of the last failure.  Nothing aborts the process.
+ */
+#ifndef DAS_H
+#define DAS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DAS_OK 0
+#define DAS_ERR_INVALID_ARG 1
+#define DAS_ERR_CUDA 2
+#define DAS_ERR_OOM 3
+#define DAS_ERR_UNSUPPORTED 4
+#define DAS_ERR_TIMEOUT 5
+
+/* CUDA stream handle (same object as cudaStream_t; NULL is the legacy default stream). */
+typedef struct CUstream_st *das_stream_t;
+
+typedef struct das_plan das_plan_t;
+
+/* Transmit kinds (Sec. 2, Eq. 1 footnote, and the photoacoustic remark). */
+enum { DAS_TX_DIVERGING = 0, DAS_TX_PLANE = 1, DAS_TX_NONE = 2 };
+
+/* Public channel-data / image element types. */
+enum {
+    DAS_SAMPLE_F32 = 0, /* real RF samples, float32; images float32 */
+    DAS_SAMPLE_C64 = 1  /* complex IQ samples, interleaved float32 (re, im); images complex64 */
+};
+
+/* Storage of the channel data inside the plan after relayout (Sec. 3.3,
+ * mixed-precision storage: 16-bit storage, float32 interpolation and sums). */
+enum {
+    DAS_STORE_F32 = 0,
+    DAS_STORE_F16 = 1, /* half, with a float32 scale per (transmit, element) */
+    DAS_STORE_BF16 = 2 /* bfloat16, with a float32 scale per (transmit, element) */
+};
+
+/* Receive array (Sec. 2: receivers r_m, each with an origin and a direction). */
+typedef struct {
+    int n_elements;          /* M >= 1 */
+    const double *positions; /* host, [M][3] metres */
+    const double *normals;   /* host, [M][3] unit vectors, or NULL for +z */
+    double t0_ref[3];        /* reference point o of the transmit time origin, metres */
+} das_geometry_t;
+
+/* Voxel grid: voxel (ix, iy, iz) at origin + spacing * (ix, iy, iz); images are
+ * stored [b][iz][iy][ix] (x fastest), voxel index n = (iz * ny + iy) * nx + ix. */
+typedef struct {
+    int nx, ny, nz;
+    double origin[3];
+    double spacing[3];
+} das_grid_t;
+
+/* One transmit (observation q). */
+typedef struct {
+    int kind;          /* DAS_TX_* */
+    double vec[3];     /* DIVERGING: virtual source (m); PLANE: unit propagation direction */
+    const float *w_tx; /* host, [N] transmit weight per voxel (Sec. 2, precomputed w^tx), or NULL for 1 */
+} das_tx_t;
+
+typedef struct {
+    int n_samples;   /* K >= 2 */
+    int sample_type; /* DAS_SAMPLE_* of the public channel data and image */
+    int storage;     /* DAS_STORE_* used inside the plan */
+    int max_batch;   /* largest batch (frames per call) the plan reserves scratch for, >= 1 */
+    int t0_offset;   /* 1: diverging-wave time origin at o (default reading); 0: paper footnote form */
+} das_options_t;
+
+/* Plan description returned by das_plan_info. */
+typedef struct {
+    long long n_voxels;       /* N */
+    int n_elements;           /* M */
+    int n_transmits;          /* Q */
+    int n_samples;            /* K */
+    int sample_type;
+    int storage;
+    int max_batch;
+    long long device_bytes;   /* device memory held by the plan */
+    double c;                 /* current speed of sound */
+    long long kernel_launches; /* kernels this plan has launched so far */
+} das_plan_info_t;
+
+/* Kernel launch shape, set by the autotuner (das_plan_set_tuning). */
+typedef struct {
+    int frames_per_thread; /* frames accumulated per thread in the forward kernel (0: automatic) */
+    int ctas_per_sm;       /* occupancy hint for persistent launches (0: automatic) */
+} das_tuning_t;
+
+/* Build a plan (Sec. 2 problem statement: grid, receivers, observations, c).
+ * c: speed of sound (m/s, > 0); fs: sampling rate (Hz, > 0); f_demod:
+ * demodulation frequency (Hz; 0 for RF); f_number: receive f-number (<= 0:
+ * full aperture).  Copies the geometry to the device and reserves scratch for
+ * options->max_batch frames.  Synchronous.  On failure *out is NULL. */
+int das_plan_create(das_plan_t **out, const das_geometry_t *geometry, const das_grid_t *grid,
+                    const das_tx_t *tx_list, int n_tx, double c, double fs, double f_demod,
+                    double f_number, const das_options_t *options);
+
+/* Release a plan and its device memory (synchronises the device).  NULL is accepted. */
+void das_plan_destroy(das_plan_t *plan);
+
+/* Change the speed of sound of the plan; the per-tile reference delays are
+ * rebuilt on the stream of the next compute call.  No allocation. */
+int das_plan_set_c(das_plan_t *plan, double c);
+
+int das_plan_info(const das_plan_t *plan, das_plan_info_t *info);
+
+int das_plan_set_tuning(das_plan_t *plan, const das_tuning_t *tuning);
+
+/* Forward DAS (Eq. 2) for `batch` frames (1 <= batch <= max_batch).
+ * y_dev: [batch][Q][M][K] samples of sample_type.  x_dev: [batch][N] image
+ * (float32 for RF, complex64 for IQ), overwritten.  Runs the relayout of the
+ * channel data into the plan's scratch (Sec. 3.2, batch-inner order, fused
+ * with the 16-bit conversion of Sec. 3.3) and the DAS kernel. */
+int das_forward(das_plan_t *plan, const void *y_dev, void *x_dev, int batch, das_stream_t stream);
+
+/* das_forward with host buffers: copies y_host to the device, runs the
+ * forward pass and copies the image back into x_host, then synchronises the
+ * stream.  Uses device staging buffers the plan reserves on first use
+ * (so the first call allocates).  Pinned host memory is fastest. */
+int das_forward_host(das_plan_t *plan, const void *y_host, void *x_host, int batch, das_stream_t stream);
+
+/* Adjoint DAS^H: the exact conjugate transpose of the linear map y -> x of
+ * das_forward.  x_dev: [batch][N] (float32 / complex64); y_dev: [batch][Q][M][K]
+ * of sample_type, overwritten (not accumulated).  For real RF data it is the
+ * transpose; a complex64 x cannot be passed to an RF plan. */
+int das_adjoint(das_plan_t *plan, const void *x_dev, void *y_dev, int batch, das_stream_t stream);
+
+/* Derivative of the image with respect to c, contracted with a cotangent:
+ * *dLdc_dev = Re sum_{b,n} conj(gx_bn) d x_bn / d c  (one double on the device).
+ * Delays are recomputed, not stored.  With gx = 2 dL/d conj(x) (the gradient
+ * PyTorch hands back for a real loss L of a complex image) this is dL/dc. */
+int das_grad_c(das_plan_t *plan, const void *y_dev, const void *gx_dev, double *dLdc_dev, int batch,
+               das_stream_t stream);
+
+/* Number of (q, m, n) terms of Eq. 2 that contribute (inside the aperture,
+ * 0 <= k <= K - 2) for the plan's current c, counted on the device with the
+ * kernels' own float32 decisions.  Synchronous; result in *count_host. */
+int das_count_active(das_plan_t *plan, long long *count_host, das_stream_t stream);
+
+/* Kernel timing for benchmarks.  With capacity > 0 the plan records a CUDA
+ * event pair around the delay-and-sum kernel of each following das_forward
+ * call, for up to `capacity` calls (capacity 0 switches it off).
+ * das_plan_timing waits for the recorded events, returns the summed kernel
+ * time in milliseconds and the number of timed launches, and starts over.
+ * Events are created in das_plan_enable_timing, not in the timed calls. */
+int das_plan_enable_timing(das_plan_t *plan, int capacity);
+int das_plan_timing(das_plan_t *plan, double *ms_total, int *launches);
+
+/* Text of the last error on the calling thread ("" if none). */
+const char *das_last_error(void);
+
+/* Library version string. */
+const char *das_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DAS_H */

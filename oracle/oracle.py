@@ -107,7 +107,7 @@ def _channels_f32(scene, y) -> np.ndarray:
     """Channel data as a contiguous float32 array ([..., 2] interleaved for IQ)."""
     a = np.asarray(y)
     if scene.iq:
-        a = np.ascontiguousarray(a.astype(np.complex64)).view(np.float32)
+        a = np.ascontiguousarray(a, dtype=np.complex64).view(np.float32)
     else:
         a = np.ascontiguousarray(a, dtype=np.float32)
     return a

@@ -1,0 +1,224 @@
+// das_adjoint.cu -- adjoint delay-and-sum (image -> channel data), the exact
+// conjugate transpose of the forward map of Eq. 2 (Sec. 2).
+//
+// Each forward term reads two samples, w e^{i theta tau} ((1 - a) y[k] + a y[k+1]);
+// its adjoint sends conj(w e^{i theta tau}) (1 - a) x_n to y[k] and
+// conj(w e^{i theta tau}) a x_n to y[k+1].  The kernel is element-major: one
+// CTA owns the channel rows (q, m) of one element m for a chunk of transmits
+// and frames, accumulates them in shared memory while it visits every voxel
+// tile that can see the element, and writes each row once, in the public
+// layout y[b][q][m][k].  No global atomics; every output value is written by
+// exactly one CTA, zeros included.
+//
+// Delays use the same split as the forward kernels (float64 reference to the
+// tile centre, float32 offsets; see das_internal.cuh).
+#include "das_internal.cuh"
+
+namespace das {
+
+constexpr int ADJ_SLOTS = 4;                 // tiles processed at once
+constexpr int ADJ_THREADS = ADJ_SLOTS * TILE_N;
+
+struct AdjTileRec {
+    float gx, gy, gz, d0;  // tile centre minus element, and its norm
+    float rf;              // fractional part of the reference delay
+    int rb;                // integer part
+    int tile;
+    int pad;
+};
+
+template <bool IQ, int FB>
+__global__ void __launch_bounds__(ADJ_THREADS, 1) adjoint_kernel(const AdjArgs A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int C = IQ ? 2 : 1;
+    const int m = blockIdx.x;
+    const int q0 = blockIdx.y * A.qc;
+    const int nq = min(A.qc, A.Q - q0);
+    const int b0 = blockIdx.z * FB;
+    const int K = A.K;
+    float *acc = reinterpret_cast<float *>(smem);                             // [qc][K][FB][C]
+    AdjTileRec *recs = reinterpret_cast<AdjTileRec *>(acc + (size_t)A.qc * K * FB * C);  // [ADJ_THREADS]
+    int *s_cnt = reinterpret_cast<int *>(recs + ADJ_THREADS);                 // [ADJ_THREADS / 32]
+
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < A.qc * K * FB * C; i += ADJ_THREADS) acc[i] = 0.f;
+
+    const GridDesc &g = A.g;
+    const double rx = A.elem_pos[3 * m], ry = A.elem_pos[3 * m + 1], rz = A.elem_pos[3 * m + 2];
+    const float4 nn = A.elem_nrm[m];
+    const long long ntiles = n_tiles(g);
+
+    const int slot = tid / TILE_N, vl = tid % TILE_N;
+    int lx, ly, lz;
+    lane_offset(vl, lx, ly, lz);
+    const float dx = (float)(g.sx * (lx - 0.5 * (TILE_X - 1)));
+    const float dy = (float)(g.sy * (ly - 0.5 * (TILE_Y - 1)));
+    const float dz = (float)(g.sz * (lz - 0.5 * (TILE_Z - 1)));
+    const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+
+    for (long long t0 = 0; t0 < ntiles; t0 += ADJ_THREADS) {
+        __syncthreads();  // records of the previous pass are no longer read (and acc is zeroed)
+        // float64 reference delay of element m to the tile centre, and a
+        // conservative test whether any voxel of the tile sees the element
+        const long long t = t0 + tid;
+        bool cand = false;
+        AdjTileRec rec;
+        if (t < ntiles) {
+            const int tx = (int)(t % g.tiles_x);
+            const int ty = (int)((t / g.tiles_x) % g.tiles_y);
+            const int tz = (int)(t / ((long long)g.tiles_x * g.tiles_y));
+            double cx, cy, cz;
+            tile_centre(g, tx, ty, tz, cx, cy, cz);
+            const double Gx = cx - rx, Gy = cy - ry, Gz = cz - rz;
+            const double D0 = sqrt(Gx * Gx + Gy * Gy + Gz * Gz);
+            const double R0 = A.ad * D0;
+            const double Rf = floor(R0);
+            rec.gx = (float)Gx; rec.gy = (float)Gy; rec.gz = (float)Gz; rec.d0 = (float)D0;
+            rec.rf = (float)(R0 - Rf);
+            rec.rb = (int)Rf;
+            rec.tile = (int)t;
+            rec.pad = 0;
+            cand = true;
+            if (A.thr >= 0.f) {
+                const float z0 = rec.gx * nn.x + rec.gy * nn.y + rec.gz * nn.z;
+                const float ux = rec.gy * nn.z - rec.gz * nn.y, uy = rec.gz * nn.x - rec.gx * nn.z,
+                            uz = rec.gx * nn.y - rec.gy * nn.x;
+                const float rho0 = sqrtf(ux * ux + uy * uy + uz * uz);
+                const float zmax = z0 + A.tile_radius;
+                const float rmin = fmaxf(rho0 - A.tile_radius, 0.f);
+                cand = (zmax > 0.f) && (rmin * rmin <= A.thr * zmax * zmax * 1.001f);
+            }
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, cand);
+        if (lane == 0) s_cnt[warp] = __popc(bal);
+        __syncthreads();
+        int off = 0, total = 0;
+        for (int w = 0; w < ADJ_THREADS / 32; ++w) {
+            const int c = s_cnt[w];
+            off += (w < warp) ? c : 0;
+            total += c;
+        }
+        if (cand) recs[off + __popc(bal & ((1u << lane) - 1u))] = rec;
+        __syncthreads();
+
+        for (int c = slot; c < total; c += ADJ_SLOTS) {
+            const AdjTileRec R = recs[c];
+            const int tile = R.tile;
+            const int tx = tile % g.tiles_x;
+            const int ty = (tile / g.tiles_x) % g.tiles_y;
+            const int tz = tile / (g.tiles_x * g.tiles_y);
+            const int ix = tx * TILE_X + lx, iy = ty * TILE_Y + ly, iz = tz * TILE_Z + lz;
+            if (ix >= g.nx || iy >= g.ny || iz >= g.nz) continue;
+            const float ex = R.gx + dx, ey = R.gy + dy, ez = R.gz + dz;
+            if (A.thr >= 0.f) {
+                const float zax = fmaf(ex, nn.x, fmaf(ey, nn.y, ez * nn.z));
+                const float ux = fmaf(ey, nn.z, -ez * nn.y), uy = fmaf(ez, nn.x, -ex * nn.z),
+                            uz = fmaf(ex, nn.y, -ey * nn.x);
+                const float rho2 = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
+                if (!((zax > 0.f) && (rho2 <= A.thr * zax * zax))) continue;
+            }
+            const long long n = ((long long)iz * g.ny + iy) * g.nx + ix;
+            const float d = sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
+            const float num = fmaf(2.f, fmaf(R.gx, dx, fmaf(R.gy, dy, R.gz * dz)), dd);
+            const float r = R.rf + A.a * __fdividef(num, d + R.d0);
+            float xr[FB], xi[FB];
+#pragma unroll
+            for (int b = 0; b < FB; ++b) {
+                xr[b] = xi[b] = 0.f;
+                if (b0 + b < A.B) {
+                    const size_t o = (size_t)(b0 + b) * g.n_voxels + n;
+                    if (IQ) {
+                        const float2 v = reinterpret_cast<const float2 *>(A.x)[o];
+                        xr[b] = v.x; xi[b] = v.y;
+                    } else {
+                        xr[b] = reinterpret_cast<const float *>(A.x)[o];
+                    }
+                }
+            }
+            for (int qq = 0; qq < nq; ++qq) {
+                const int q = q0 + qq;
+                const size_t tq = (size_t)tile * A.Q + q;
+                const float f = r + __ldg(A.tx_t + tq * TILE_N + vl);
+                const float fl = floorf(f);
+                const float al = f - fl;
+                const int k = __ldg(A.tx_tb + tq) + R.rb + (int)fl;
+                if ((unsigned)k > (unsigned)(K - 2)) continue;
+                const float w = A.w_tx ? __ldg(A.w_tx + tq * TILE_N + vl) : 1.f;
+                float *a0 = acc + ((size_t)qq * K + k) * FB * C;
+                float *a1 = a0 + FB * C;
+                if constexpr (IQ) {
+                    float sn, cs;
+                    __sincosf(A.theta * (al - 0.5f), &sn, &cs);
+                    const float uhr = cs * A.hr - sn * A.hi, uhi = cs * A.hi + sn * A.hr;
+                    const float ubr = cs * A.hr + sn * A.hi, ubi = sn * A.hr - cs * A.hi;
+                    const float w0 = w * (1.f - al), w1 = w * al;
+                    // conjugated coefficients of the two taps (pre-rotated sample domain)
+                    const float c0r = w0 * uhr, c0i = -w0 * uhi, c1r = w1 * ubr, c1i = -w1 * ubi;
+#pragma unroll
+                    for (int b = 0; b < FB; ++b) {
+                        atomicAdd(a0 + 2 * b, c0r * xr[b] - c0i * xi[b]);
+                        atomicAdd(a0 + 2 * b + 1, c0r * xi[b] + c0i * xr[b]);
+                        atomicAdd(a1 + 2 * b, c1r * xr[b] - c1i * xi[b]);
+                        atomicAdd(a1 + 2 * b + 1, c1r * xi[b] + c1i * xr[b]);
+                    }
+                } else {
+                    const float w0 = w * (1.f - al), w1 = w * al;
+#pragma unroll
+                    for (int b = 0; b < FB; ++b) {
+                        atomicAdd(a0 + b, w0 * xr[b]);
+                        atomicAdd(a1 + b, w1 * xr[b]);
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    // Write the owned rows in the public layout; IQ rows leave the pre-rotated
+    // domain through conj(e^{i theta k}).
+    for (int qq = 0; qq < nq; ++qq) {
+        const int q = q0 + qq;
+        for (int b = 0; b < FB; ++b) {
+            if (b0 + b >= A.B) break;
+            const size_t row = (((size_t)(b0 + b) * A.Q + q) * A.M + m) * (size_t)K;
+            for (int k = tid; k < K; k += ADJ_THREADS) {
+                const float *a = acc + ((size_t)qq * K + k) * FB * C + b * C;
+                if constexpr (IQ) {
+                    const float2 rt = A.rot ? A.rot[k] : make_float2(1.f, 0.f);
+                    reinterpret_cast<float2 *>(A.y)[row + k] =
+                        make_float2(a[0] * rt.x + a[1] * rt.y, a[1] * rt.x - a[0] * rt.y);
+                } else {
+                    reinterpret_cast<float *>(A.y)[row + k] = a[0];
+                }
+            }
+        }
+    }
+}
+
+size_t adjoint_smem_bytes(int qc, int K, int fb, int iq) {
+    return sizeof(float) * (size_t)qc * K * fb * (iq ? 2 : 1) + sizeof(AdjTileRec) * ADJ_THREADS +
+           sizeof(int) * (ADJ_THREADS / 32);
+}
+
+template <bool IQ, int FB>
+static cudaError_t launch_adj_t(const AdjArgs &A, cudaStream_t s) {
+    const size_t smem = adjoint_smem_bytes(A.qc, A.K, FB, IQ);
+    auto kern = adjoint_kernel<IQ, FB>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)A.M, (unsigned)((A.Q + A.qc - 1) / A.qc), (unsigned)((A.B + FB - 1) / FB));
+    kern<<<grid, ADJ_THREADS, smem, s>>>(A);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint(const AdjArgs &A, int iq, cudaStream_t s) {
+    switch (A.fb) {
+    case 1: return iq ? launch_adj_t<true, 1>(A, s) : launch_adj_t<false, 1>(A, s);
+    case 2: return iq ? launch_adj_t<true, 2>(A, s) : launch_adj_t<false, 2>(A, s);
+    case 4: return iq ? launch_adj_t<true, 4>(A, s) : launch_adj_t<false, 4>(A, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace das

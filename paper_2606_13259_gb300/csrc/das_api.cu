@@ -1,0 +1,655 @@
+// das_api.cu -- the C-ABI of include/das.h: plan construction (geometry to the
+// device, per-tile transmit tables), argument checking, scratch management and
+// kernel dispatch.  See das.h for the contract of every entry point.
+#include "das.h"
+#include "das_internal.cuh"
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+using namespace das;
+
+static thread_local char g_err[1024];
+
+static int fail(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+static int cuda_fail(cudaError_t e, const char *what) {
+    const int code = (e == cudaErrorMemoryAllocation) ? DAS_ERR_OOM : DAS_ERR_CUDA;
+    return fail(code, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+#define DAS_CU(call)                                                 \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);          \
+    } while (0)
+
+struct das_plan {
+    int device = 0;
+    GridDesc g{};
+    int M = 0, Q = 0, K = 0;
+    int sample_type = 0, storage = 0, max_batch = 1, t0_offset = 1;
+    double c = 0, fs = 0, f_demod = 0, f_number = 0;
+    double t0[3] = {0, 0, 0};
+    bool has_w = false;
+    double *elem_pos = nullptr;
+    float4 *elem_nrm = nullptr;
+    int *tx_kind = nullptr;
+    double *tx_vec = nullptr;
+    double *tx_off = nullptr;
+    int *tx_tb = nullptr;
+    float *tx_t = nullptr;
+    float *w_tx = nullptr;
+    float2 *rot = nullptr;
+    float *scale = nullptr;
+    float *inv_scale = nullptr;
+    void *z = nullptr;
+    size_t z_bytes = 0;
+    double *partial = nullptr;
+    size_t partial_n = 0;
+    double *scalar = nullptr;
+    void *stage_y = nullptr;
+    void *stage_x = nullptr;
+    bool dirty = true;
+    das_tuning_t tuning{0, 0};
+    size_t bytes = 0;
+    long long launches = 0;
+    std::vector<cudaEvent_t> ev_start, ev_stop;
+    int ev_used = 0;
+    std::vector<void *> allocs;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int dalloc(das_plan *p, void **ptr, size_t bytes, const char *what) {
+    *ptr = nullptr;
+    if (bytes == 0) return DAS_OK;
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? DAS_ERR_OOM : DAS_ERR_CUDA, "cudaMalloc(%zu bytes) for %s: %s",
+                    bytes, what, cudaGetErrorString(e));
+    }
+    p->allocs.push_back(*ptr);
+    p->bytes += bytes;
+    return DAS_OK;
+}
+
+void dfree(das_plan *p, void *ptr) {
+    if (!ptr) return;
+    for (size_t i = 0; i < p->allocs.size(); ++i)
+        if (p->allocs[i] == ptr) { p->allocs.erase(p->allocs.begin() + i); break; }
+    cudaFree(ptr);
+}
+
+bool is_iq(const das_plan *p) { return p->sample_type == DAS_SAMPLE_C64; }
+
+int sample_bytes_public(const das_plan *p) { return is_iq(p) ? 8 : 4; }
+
+int sample_bytes_store(const das_plan *p) {
+    const int comp = is_iq(p) ? 2 : 1;
+    return comp * (p->storage == DAS_STORE_F32 ? 4 : 2);
+}
+
+const int FB_F32[] = {20, 16, 12, 8, 4, 2, 1};
+const int FB_16[] = {24, 20, 16, 12, 8, 4, 2, 1};
+
+// Frames per thread for a call with B frames: the supported value minimising
+// chunks * (geometry overhead + frames per chunk), ties to the larger.
+int choose_fb(const das_plan *p, int B, int mode) {
+    const int store = p->storage;
+    if (p->tuning.frames_per_thread > 0 && tile_fb_supported(mode, is_iq(p), store, p->tuning.frames_per_thread))
+        return p->tuning.frames_per_thread;
+    const int *list = (store == DAS_STORE_F32 || mode != MODE_FWD) ? FB_F32 : FB_16;
+    const int nl = (store == DAS_STORE_F32 || mode != MODE_FWD) ? 7 : 8;
+    const int overhead = 6;
+    int best = 1;
+    long best_cost = -1;
+    for (int i = 0; i < nl; ++i) {
+        const int fb = list[i];
+        if (!tile_fb_supported(mode, is_iq(p), store, fb)) continue;
+        const long chunks = (B + fb - 1) / fb;
+        const long cost = chunks * (overhead + fb);
+        if (best_cost < 0 || cost < best_cost) { best_cost = cost; best = fb; }
+    }
+    return best;
+}
+
+int padded_batch(const das_plan *p, int B, int mode) {
+    const int fb = choose_fb(p, B, mode);
+    return ((B + fb - 1) / fb) * fb;
+}
+
+size_t scratch_bytes_for(const das_plan *p) {
+    int bs = 1;
+    for (int B = 1; B <= p->max_batch; ++B) {
+        const int a = padded_batch(p, B, MODE_FWD);
+        const int b = p->storage == DAS_STORE_F32 ? padded_batch(p, B, MODE_DC) : 1;
+        bs = a > bs ? a : bs;
+        bs = b > bs ? b : bs;
+    }
+    return (size_t)p->Q * p->M * p->K * (size_t)bs * sample_bytes_store(p);
+}
+
+int ensure_scratch(das_plan *p) {
+    const size_t need = scratch_bytes_for(p);
+    if (need <= p->z_bytes) return DAS_OK;
+    dfree(p, p->z);
+    p->bytes -= p->z_bytes;
+    p->z = nullptr;
+    p->z_bytes = 0;
+    int rc = dalloc(p, &p->z, need, "channel-data scratch");
+    if (rc != DAS_OK) return rc;
+    p->z_bytes = need;
+    return DAS_OK;
+}
+
+int prepare_if_dirty(das_plan *p, cudaStream_t s) {
+    if (!p->dirty) return DAS_OK;
+    DAS_CU(launch_prepare(p->g, p->Q, p->tx_kind, p->tx_vec, p->tx_off, p->t0, p->fs / p->c, p->tx_tb, p->tx_t, s));
+    p->launches += 1;
+    p->dirty = false;
+    return DAS_OK;
+}
+
+void destroy_events(das_plan *p) {
+    for (cudaEvent_t e : p->ev_start) cudaEventDestroy(e);
+    for (cudaEvent_t e : p->ev_stop) cudaEventDestroy(e);
+    p->ev_start.clear();
+    p->ev_stop.clear();
+    p->ev_used = 0;
+}
+
+void fill_common(const das_plan *p, float &a, double &ad, float &theta, float &hr, float &hi, float &thr, float &rad) {
+    ad = p->fs / p->c;
+    a = (float)ad;
+    const double th = 2.0 * M_PI * p->f_demod / p->fs;
+    theta = (float)th;
+    hr = (float)cos(0.5 * th);
+    hi = (float)sin(0.5 * th);
+    thr = p->f_number > 0 ? (float)((1.0 + 1e-6) / (4.0 * p->f_number * p->f_number)) : -1.f;
+    const double rx = 0.5 * (TILE_X - 1) * p->g.sx, ry = 0.5 * (TILE_Y - 1) * p->g.sy,
+                 rz = 0.5 * (TILE_Z - 1) * p->g.sz;
+    rad = (float)(sqrt(rx * rx + ry * ry + rz * rz) * (1.0 + 1e-4) + 1e-9);
+}
+
+TileArgs tile_args(const das_plan *p, int Bs, int B, int fb, const void *z) {
+    TileArgs A{};
+    A.g = p->g;
+    A.M = p->M;
+    A.Q = p->Q;
+    A.K = p->K;
+    A.Bs = Bs;
+    A.B = B;
+    A.fb = fb;
+    fill_common(p, A.a, A.ad, A.theta, A.hr, A.hi, A.thr, A.tile_radius);
+    A.inv_c = 1.0 / p->c;
+    A.elem_pos = p->elem_pos;
+    A.elem_nrm = p->elem_nrm;
+    A.tx_tb = p->tx_tb;
+    A.tx_t = p->tx_t;
+    A.w_tx = p->w_tx;
+    A.scale = p->storage == DAS_STORE_F32 ? nullptr : p->scale;
+    A.z = z;
+    return A;
+}
+
+bool aligned(const void *ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
+
+// Relayout of the public channel data into the plan scratch (or the data
+// itself when the layouts coincide).  Returns the pointer the kernels read.
+int stage_channels(das_plan *p, const void *y, int B, int Bs, cudaStream_t s, const void **z_out) {
+    const bool iq = is_iq(p);
+    const int QM = p->Q * p->M;
+    if (p->storage != DAS_STORE_F32) {
+        DAS_CU(launch_scale(y, p->scale, p->inv_scale, iq, p->storage, B, QM, p->K, s));
+        p->launches += 1;
+    }
+    if (!iq && p->storage == DAS_STORE_F32 && Bs == 1) {
+        *z_out = y;
+        return DAS_OK;
+    }
+    const size_t need = (size_t)QM * p->K * (size_t)Bs * sample_bytes_store(p);
+    if (need > p->z_bytes) return fail(DAS_ERR_INVALID_ARG, "batch needs %zu bytes of scratch, plan holds %zu", need, p->z_bytes);
+    DAS_CU(launch_relayout(y, p->z, iq ? p->rot : nullptr, p->storage == DAS_STORE_F32 ? nullptr : p->inv_scale, iq,
+                           p->storage, B, Bs, QM, p->K, s));
+    p->launches += 1;
+    *z_out = p->z;
+    return DAS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *das_last_error(void) { return g_err; }
+
+const char *das_version(void) { return "das-gb300 0.1.0 (sm_103a)"; }
+
+int das_plan_create(das_plan_t **out, const das_geometry_t *geometry, const das_grid_t *grid,
+                    const das_tx_t *tx_list, int n_tx, double c, double fs, double f_demod, double f_number,
+                    const das_options_t *options) {
+    g_err[0] = 0;
+    if (!out) return fail(DAS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!geometry || !grid || !tx_list || !options) return fail(DAS_ERR_INVALID_ARG, "NULL argument");
+    if (geometry->n_elements < 1 || !geometry->positions) return fail(DAS_ERR_INVALID_ARG, "need >= 1 element with positions");
+    if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return fail(DAS_ERR_INVALID_ARG, "grid dimensions must be >= 1");
+    for (int i = 0; i < 3; ++i)
+        if (!(grid->spacing[i] > 0) || !std::isfinite(grid->spacing[i]) || !std::isfinite(grid->origin[i]))
+            return fail(DAS_ERR_INVALID_ARG, "grid spacing must be positive and finite");
+    if (n_tx < 1) return fail(DAS_ERR_INVALID_ARG, "need >= 1 transmit");
+    if (n_tx > 128) return fail(DAS_ERR_UNSUPPORTED, "at most 128 transmits per plan (got %d)", n_tx);
+    if (!(c > 0) || !std::isfinite(c)) return fail(DAS_ERR_INVALID_ARG, "c must be positive");
+    if (!(fs > 0) || !std::isfinite(fs)) return fail(DAS_ERR_INVALID_ARG, "fs must be positive");
+    if (!(f_demod >= 0) || !std::isfinite(f_demod)) return fail(DAS_ERR_INVALID_ARG, "f_demod must be >= 0");
+    if (!std::isfinite(f_number)) return fail(DAS_ERR_INVALID_ARG, "f_number must be finite");
+    if (options->n_samples < 2) return fail(DAS_ERR_INVALID_ARG, "n_samples must be >= 2");
+    if (options->sample_type != DAS_SAMPLE_F32 && options->sample_type != DAS_SAMPLE_C64)
+        return fail(DAS_ERR_INVALID_ARG, "unknown sample_type %d", options->sample_type);
+    if (options->storage < DAS_STORE_F32 || options->storage > DAS_STORE_BF16)
+        return fail(DAS_ERR_INVALID_ARG, "unknown storage %d", options->storage);
+    if (options->max_batch < 1) return fail(DAS_ERR_INVALID_ARG, "max_batch must be >= 1");
+    if (options->sample_type == DAS_SAMPLE_F32 && f_demod != 0.0)
+        return fail(DAS_ERR_INVALID_ARG, "real RF data (DAS_SAMPLE_F32) need f_demod = 0");
+    const long long N = (long long)grid->nx * grid->ny * grid->nz;
+    if (N > (1LL << 40)) return fail(DAS_ERR_UNSUPPORTED, "grid too large");
+
+    for (int m = 0; m < geometry->n_elements; ++m) {
+        double len2 = 0;
+        for (int i = 0; i < 3; ++i) {
+            if (!std::isfinite(geometry->positions[3 * m + i])) return fail(DAS_ERR_INVALID_ARG, "element %d position not finite", m);
+            const double v = geometry->normals ? geometry->normals[3 * m + i] : (i == 2 ? 1.0 : 0.0);
+            len2 += v * v;
+        }
+        if (!(fabs(sqrt(len2) - 1.0) <= 1e-6)) return fail(DAS_ERR_INVALID_ARG, "element %d normal is not a unit vector", m);
+    }
+    for (int q = 0; q < n_tx; ++q) {
+        const int kd = tx_list[q].kind;
+        if (kd < DAS_TX_DIVERGING || kd > DAS_TX_NONE) return fail(DAS_ERR_INVALID_ARG, "transmit %d: unknown kind %d", q, kd);
+        double l2 = 0;
+        for (int i = 0; i < 3; ++i) {
+            if (!std::isfinite(tx_list[q].vec[i])) return fail(DAS_ERR_INVALID_ARG, "transmit %d: vector not finite", q);
+            l2 += tx_list[q].vec[i] * tx_list[q].vec[i];
+        }
+        if (kd == DAS_TX_PLANE && !(fabs(sqrt(l2) - 1.0) <= 1e-6))
+            return fail(DAS_ERR_INVALID_ARG, "transmit %d: plane direction is not a unit vector", q);
+    }
+
+    das_plan *p = new (std::nothrow) das_plan();
+    if (!p) return fail(DAS_ERR_OOM, "host allocation failed");
+    auto bail = [&](int rc) {
+        for (void *a : p->allocs) cudaFree(a);
+        delete p;
+        return rc;
+    };
+    if (cudaGetDevice(&p->device) != cudaSuccess) { cudaGetLastError(); return bail(fail(DAS_ERR_CUDA, "no CUDA device")); }
+
+    GridDesc &g = p->g;
+    g.nx = grid->nx; g.ny = grid->ny; g.nz = grid->nz;
+    g.tiles_x = (grid->nx + TILE_X - 1) / TILE_X;
+    g.tiles_y = (grid->ny + TILE_Y - 1) / TILE_Y;
+    g.tiles_z = (grid->nz + TILE_Z - 1) / TILE_Z;
+    g.n_voxels = N;
+    g.ox = grid->origin[0]; g.oy = grid->origin[1]; g.oz = grid->origin[2];
+    g.sx = grid->spacing[0]; g.sy = grid->spacing[1]; g.sz = grid->spacing[2];
+    if (n_tiles(g) > 0x7fffffffLL) return bail(fail(DAS_ERR_UNSUPPORTED, "too many voxel tiles"));
+    p->M = geometry->n_elements;
+    p->Q = n_tx;
+    p->K = options->n_samples;
+    p->sample_type = options->sample_type;
+    p->storage = options->storage;
+    p->max_batch = options->max_batch;
+    p->t0_offset = options->t0_offset ? 1 : 0;
+    p->c = c; p->fs = fs; p->f_demod = f_demod; p->f_number = f_number;
+    for (int i = 0; i < 3; ++i) p->t0[i] = geometry->t0_ref[i];
+
+    // host copies of the geometry
+    const int M = p->M, Q = p->Q;
+    std::vector<double> pos(3 * (size_t)M);
+    std::vector<float4> nrm(M);
+    for (int m = 0; m < M; ++m) {
+        double n[3] = {0, 0, 1};
+        for (int i = 0; i < 3; ++i) {
+            pos[3 * m + i] = geometry->positions[3 * m + i];
+            if (!std::isfinite(pos[3 * m + i])) return bail(fail(DAS_ERR_INVALID_ARG, "element %d position not finite", m));
+            if (geometry->normals) n[i] = geometry->normals[3 * m + i];
+        }
+        const double len = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        if (!(len > 0) || fabs(len - 1.0) > 1e-6) return bail(fail(DAS_ERR_INVALID_ARG, "element %d normal is not a unit vector", m));
+        nrm[m] = make_float4((float)n[0], (float)n[1], (float)n[2], 0.f);
+    }
+    std::vector<int> kind(Q);
+    std::vector<double> vec(3 * (size_t)Q), off(Q, 0.0);
+    for (int q = 0; q < Q; ++q) {
+        kind[q] = tx_list[q].kind;
+        if (kind[q] < DAS_TX_DIVERGING || kind[q] > DAS_TX_NONE) return bail(fail(DAS_ERR_INVALID_ARG, "transmit %d: unknown kind", q));
+        for (int i = 0; i < 3; ++i) {
+            vec[3 * q + i] = tx_list[q].vec[i];
+            if (!std::isfinite(vec[3 * q + i])) return bail(fail(DAS_ERR_INVALID_ARG, "transmit %d: vector not finite", q));
+        }
+        if (kind[q] == DAS_TX_PLANE) {
+            const double l = sqrt(vec[3 * q] * vec[3 * q] + vec[3 * q + 1] * vec[3 * q + 1] + vec[3 * q + 2] * vec[3 * q + 2]);
+            if (fabs(l - 1.0) > 1e-6) return bail(fail(DAS_ERR_INVALID_ARG, "transmit %d: plane direction is not a unit vector", q));
+        }
+        if (kind[q] == DAS_TX_DIVERGING && p->t0_offset) {
+            const double dx = vec[3 * q] - p->t0[0], dy = vec[3 * q + 1] - p->t0[1], dz = vec[3 * q + 2] - p->t0[2];
+            off[q] = sqrt(dx * dx + dy * dy + dz * dz);
+        }
+        if (tx_list[q].w_tx) p->has_w = true;
+    }
+
+    const long long T = n_tiles(g);
+    int rc;
+#define DAS_ALLOC(ptr, bytes, what) \
+    if ((rc = dalloc(p, (void **)&(ptr), (bytes), (what))) != DAS_OK) return bail(rc)
+    DAS_ALLOC(p->elem_pos, sizeof(double) * 3 * M, "element positions");
+    DAS_ALLOC(p->elem_nrm, sizeof(float4) * M, "element normals");
+    DAS_ALLOC(p->tx_kind, sizeof(int) * Q, "transmit kinds");
+    DAS_ALLOC(p->tx_vec, sizeof(double) * 3 * Q, "transmit vectors");
+    DAS_ALLOC(p->tx_off, sizeof(double) * Q, "transmit offsets");
+    DAS_ALLOC(p->tx_tb, sizeof(int) * (size_t)T * Q, "transmit bases");
+    DAS_ALLOC(p->tx_t, sizeof(float) * (size_t)T * Q * TILE_N, "transmit delays");
+    DAS_ALLOC(p->partial, sizeof(double) * (size_t)T * p->max_batch, "partials");
+    DAS_ALLOC(p->scalar, sizeof(double), "scalar");
+    p->partial_n = (size_t)T * p->max_batch;
+    if (p->storage != DAS_STORE_F32) {
+        DAS_ALLOC(p->scale, sizeof(float) * (size_t)Q * M, "storage scale");
+        DAS_ALLOC(p->inv_scale, sizeof(float) * (size_t)Q * M, "storage inverse scale");
+    }
+    if (is_iq(p) && f_demod != 0.0) DAS_ALLOC(p->rot, sizeof(float2) * p->K, "rotation table");
+    if ((rc = ensure_scratch(p)) != DAS_OK) return bail(rc);
+
+    cudaError_t e;
+#define DAS_UP(dst, src, bytes) \
+    if ((e = cudaMemcpy((dst), (src), (bytes), cudaMemcpyHostToDevice)) != cudaSuccess) return bail(cuda_fail(e, "upload"))
+    DAS_UP(p->elem_pos, pos.data(), sizeof(double) * 3 * M);
+    DAS_UP(p->elem_nrm, nrm.data(), sizeof(float4) * M);
+    DAS_UP(p->tx_kind, kind.data(), sizeof(int) * Q);
+    DAS_UP(p->tx_vec, vec.data(), sizeof(double) * 3 * Q);
+    DAS_UP(p->tx_off, off.data(), sizeof(double) * Q);
+    if (p->rot) {
+        // e^{i 2 pi (f_d / fs) k}, reduced to one turn in float64
+        std::vector<float2> rot(p->K);
+        const double ratio = f_demod / fs;
+        for (int k = 0; k < p->K; ++k) {
+            double turns = ratio * k;
+            turns -= floor(turns);
+            rot[k] = make_float2((float)cos(2.0 * M_PI * turns), (float)sin(2.0 * M_PI * turns));
+        }
+        DAS_UP(p->rot, rot.data(), sizeof(float2) * p->K);
+    }
+    if (p->has_w) {
+        DAS_ALLOC(p->w_tx, sizeof(float) * (size_t)T * Q * TILE_N, "transmit weights");
+        std::vector<float> w((size_t)T * Q * TILE_N, 0.f);
+        for (long long t = 0; t < T; ++t) {
+            const int tx = (int)(t % g.tiles_x), ty = (int)((t / g.tiles_x) % g.tiles_y),
+                      tz = (int)(t / ((long long)g.tiles_x * g.tiles_y));
+            for (int l = 0; l < TILE_N; ++l) {
+                int lx, ly, lz;
+                lane_offset(l, lx, ly, lz);
+                const int ix = tx * TILE_X + lx, iy = ty * TILE_Y + ly, iz = tz * TILE_Z + lz;
+                if (ix >= g.nx || iy >= g.ny || iz >= g.nz) continue;
+                const long long n = ((long long)iz * g.ny + iy) * g.nx + ix;
+                for (int q = 0; q < Q; ++q)
+                    w[((size_t)t * Q + q) * TILE_N + l] = tx_list[q].w_tx ? tx_list[q].w_tx[n] : 1.f;
+            }
+        }
+        DAS_UP(p->w_tx, w.data(), sizeof(float) * w.size());
+    }
+    rc = prepare_if_dirty(p, nullptr);
+    if (rc != DAS_OK) return bail(rc);
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bail(cuda_fail(e, "plan preparation"));
+    *out = p;
+    return DAS_OK;
+#undef DAS_ALLOC
+#undef DAS_UP
+}
+
+void das_plan_destroy(das_plan_t *plan) {
+    if (!plan) return;
+    DeviceGuard guard(plan->device);
+    cudaDeviceSynchronize();
+    destroy_events(plan);
+    for (void *a : plan->allocs) cudaFree(a);
+    delete plan;
+}
+
+int das_plan_set_c(das_plan_t *plan, double c) {
+    if (!plan) return fail(DAS_ERR_INVALID_ARG, "plan is NULL");
+    if (!(c > 0) || !std::isfinite(c)) return fail(DAS_ERR_INVALID_ARG, "c must be positive");
+    if (c != plan->c) {
+        plan->c = c;
+        plan->dirty = true;
+    }
+    return DAS_OK;
+}
+
+int das_plan_info(const das_plan_t *plan, das_plan_info_t *info) {
+    if (!plan || !info) return fail(DAS_ERR_INVALID_ARG, "NULL argument");
+    info->n_voxels = plan->g.n_voxels;
+    info->n_elements = plan->M;
+    info->n_transmits = plan->Q;
+    info->n_samples = plan->K;
+    info->sample_type = plan->sample_type;
+    info->storage = plan->storage;
+    info->max_batch = plan->max_batch;
+    info->device_bytes = (long long)plan->bytes;
+    info->c = plan->c;
+    info->kernel_launches = plan->launches;
+    return DAS_OK;
+}
+
+int das_plan_enable_timing(das_plan_t *plan, int capacity) {
+    if (!plan || capacity < 0) return fail(DAS_ERR_INVALID_ARG, "bad argument");
+    DeviceGuard guard(plan->device);
+    destroy_events(plan);
+    for (int i = 0; i < capacity; ++i) {
+        cudaEvent_t a, b;
+        DAS_CU(cudaEventCreate(&a));
+        if (cudaEventCreate(&b) != cudaSuccess) {
+            cudaEventDestroy(a);
+            return cuda_fail(cudaGetLastError(), "cudaEventCreate");
+        }
+        plan->ev_start.push_back(a);
+        plan->ev_stop.push_back(b);
+    }
+    return DAS_OK;
+}
+
+int das_plan_timing(das_plan_t *plan, double *ms_total, int *launches) {
+    if (!plan || !ms_total || !launches) return fail(DAS_ERR_INVALID_ARG, "NULL argument");
+    DeviceGuard guard(plan->device);
+    double total = 0.0;
+    for (int i = 0; i < plan->ev_used; ++i) {
+        DAS_CU(cudaEventSynchronize(plan->ev_stop[i]));
+        float ms = 0.f;
+        DAS_CU(cudaEventElapsedTime(&ms, plan->ev_start[i], plan->ev_stop[i]));
+        total += ms;
+    }
+    *ms_total = total;
+    *launches = plan->ev_used;
+    plan->ev_used = 0;
+    return DAS_OK;
+}
+
+int das_plan_set_tuning(das_plan_t *plan, const das_tuning_t *tuning) {
+    if (!plan || !tuning) return fail(DAS_ERR_INVALID_ARG, "NULL argument");
+    if (tuning->frames_per_thread < 0 || tuning->ctas_per_sm < 0) return fail(DAS_ERR_INVALID_ARG, "negative tuning value");
+    if (tuning->frames_per_thread > 0 &&
+        !tile_fb_supported(MODE_FWD, is_iq(plan), plan->storage, tuning->frames_per_thread))
+        return fail(DAS_ERR_UNSUPPORTED, "frames_per_thread %d not compiled for this storage", tuning->frames_per_thread);
+    DeviceGuard guard(plan->device);
+    plan->tuning = *tuning;
+    return ensure_scratch(plan);
+}
+
+static int check_call(das_plan_t *plan, const void *a, const void *b, int batch) {
+    if (!plan) return fail(DAS_ERR_INVALID_ARG, "plan is NULL");
+    if (!a || !b) return fail(DAS_ERR_INVALID_ARG, "NULL data pointer");
+    if (batch < 1 || batch > plan->max_batch)
+        return fail(DAS_ERR_INVALID_ARG, "batch %d outside 1..max_batch (%d)", batch, plan->max_batch);
+    const size_t al = is_iq(plan) ? 8 : 4;
+    if (!aligned(a, al) || !aligned(b, al)) return fail(DAS_ERR_INVALID_ARG, "data pointers must be %zu-byte aligned", al);
+    return DAS_OK;
+}
+
+int das_forward(das_plan_t *plan, const void *y_dev, void *x_dev, int batch, das_stream_t stream) {
+    g_err[0] = 0;
+    int rc = check_call(plan, y_dev, x_dev, batch);
+    if (rc != DAS_OK) return rc;
+    DeviceGuard guard(plan->device);
+    if (!guard.ok) return fail(DAS_ERR_CUDA, "cannot select the plan's device");
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((rc = prepare_if_dirty(plan, s)) != DAS_OK) return rc;
+    const int fb = choose_fb(plan, batch, MODE_FWD);
+    const int nch = (batch + fb - 1) / fb;
+    const int Bs = nch * fb;
+    const void *z = nullptr;
+    if ((rc = stage_channels(plan, y_dev, batch, Bs, s, &z)) != DAS_OK) return rc;
+    TileArgs A = tile_args(plan, Bs, batch, fb, z);
+    A.x = x_dev;
+    const bool timed = plan->ev_used < (int)plan->ev_start.size();
+    if (timed) DAS_CU(cudaEventRecord(plan->ev_start[plan->ev_used], s));
+    DAS_CU(launch_tile(A, MODE_FWD, is_iq(plan), plan->storage, fb, nch, s));
+    plan->launches += 1;
+    if (timed) {
+        DAS_CU(cudaEventRecord(plan->ev_stop[plan->ev_used], s));
+        plan->ev_used += 1;
+    }
+    return DAS_OK;
+}
+
+int das_forward_host(das_plan_t *plan, const void *y_host, void *x_host, int batch, das_stream_t stream) {
+    g_err[0] = 0;
+    int rc = check_call(plan, y_host, x_host, batch);
+    if (rc != DAS_OK) return rc;
+    DeviceGuard guard(plan->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t ybytes = (size_t)plan->max_batch * plan->Q * plan->M * plan->K * sample_bytes_public(plan);
+    const size_t xbytes = (size_t)plan->max_batch * plan->g.n_voxels * sample_bytes_public(plan);
+    if (!plan->stage_y && (rc = dalloc(plan, &plan->stage_y, ybytes, "host-call input staging")) != DAS_OK) return rc;
+    if (!plan->stage_x && (rc = dalloc(plan, &plan->stage_x, xbytes, "host-call output staging")) != DAS_OK) return rc;
+    const size_t yb = (size_t)batch * plan->Q * plan->M * plan->K * sample_bytes_public(plan);
+    const size_t xb = (size_t)batch * plan->g.n_voxels * sample_bytes_public(plan);
+    DAS_CU(cudaMemcpyAsync(plan->stage_y, y_host, yb, cudaMemcpyHostToDevice, s));
+    if ((rc = das_forward(plan, plan->stage_y, plan->stage_x, batch, stream)) != DAS_OK) return rc;
+    DAS_CU(cudaMemcpyAsync(x_host, plan->stage_x, xb, cudaMemcpyDeviceToHost, s));
+    DAS_CU(cudaStreamSynchronize(s));
+    return DAS_OK;
+}
+
+int das_adjoint(das_plan_t *plan, const void *x_dev, void *y_dev, int batch, das_stream_t stream) {
+    g_err[0] = 0;
+    int rc = check_call(plan, x_dev, y_dev, batch);
+    if (rc != DAS_OK) return rc;
+    DeviceGuard guard(plan->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((rc = prepare_if_dirty(plan, s)) != DAS_OK) return rc;
+    const bool iq = is_iq(plan);
+    const size_t esz = iq ? 8 : 4;
+    const size_t budget = 180 * 1024;
+    int fb = 1, qc = 0;
+    const int fbs[3] = {4, 2, 1};
+    for (int i = 0; i < 3; ++i) {
+        const int f = fbs[i];
+        if (f > 1 && f > batch) continue;
+        const size_t row = (size_t)plan->K * f * esz;
+        const int qmax = (int)(budget / row);
+        if (qmax >= (plan->Q < 4 ? plan->Q : 4) || (f == 1 && qmax >= 1)) { fb = f; qc = qmax; break; }
+    }
+    if (qc < 1) return fail(DAS_ERR_UNSUPPORTED, "n_samples %d too large for the adjoint's shared-memory rows", plan->K);
+    const int nqc = (plan->Q + qc - 1) / qc;
+    qc = (plan->Q + nqc - 1) / nqc;
+    AdjArgs A{};
+    A.g = plan->g;
+    A.M = plan->M;
+    A.Q = plan->Q;
+    A.K = plan->K;
+    A.B = batch;
+    A.qc = qc;
+    A.fb = fb;
+    fill_common(plan, A.a, A.ad, A.theta, A.hr, A.hi, A.thr, A.tile_radius);
+    A.elem_pos = plan->elem_pos;
+    A.elem_nrm = plan->elem_nrm;
+    A.tx_tb = plan->tx_tb;
+    A.tx_t = plan->tx_t;
+    A.w_tx = plan->w_tx;
+    A.rot = plan->rot;
+    A.x = x_dev;
+    A.y = y_dev;
+    DAS_CU(launch_adjoint(A, iq, s));
+    plan->launches += 1;
+    return DAS_OK;
+}
+
+int das_grad_c(das_plan_t *plan, const void *y_dev, const void *gx_dev, double *dLdc_dev, int batch,
+               das_stream_t stream) {
+    g_err[0] = 0;
+    int rc = check_call(plan, y_dev, gx_dev, batch);
+    if (rc != DAS_OK) return rc;
+    if (!dLdc_dev || !aligned(dLdc_dev, 8)) return fail(DAS_ERR_INVALID_ARG, "dLdc_dev must be an aligned device double");
+    if (plan->storage != DAS_STORE_F32) return fail(DAS_ERR_UNSUPPORTED, "das_grad_c needs float32 storage");
+    DeviceGuard guard(plan->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((rc = prepare_if_dirty(plan, s)) != DAS_OK) return rc;
+    const int fb = choose_fb(plan, batch, MODE_DC);
+    const int nch = (batch + fb - 1) / fb;
+    const int Bs = nch * fb;
+    const void *z = nullptr;
+    if ((rc = stage_channels(plan, y_dev, batch, Bs, s, &z)) != DAS_OK) return rc;
+    TileArgs A = tile_args(plan, Bs, batch, fb, z);
+    A.gx = gx_dev;
+    A.partial = plan->partial;
+    const long long np = n_tiles(plan->g) * nch;
+    if ((size_t)np > plan->partial_n) return fail(DAS_ERR_INVALID_ARG, "partial buffer too small");
+    DAS_CU(launch_tile(A, MODE_DC, is_iq(plan), DAS_STORE_F32, fb, nch, s));
+    DAS_CU(launch_reduce(plan->partial, np, dLdc_dev, s));
+    plan->launches += 2;
+    return DAS_OK;
+}
+
+int das_count_active(das_plan_t *plan, long long *count_host, das_stream_t stream) {
+    g_err[0] = 0;
+    if (!plan || !count_host) return fail(DAS_ERR_INVALID_ARG, "NULL argument");
+    DeviceGuard guard(plan->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc;
+    if ((rc = prepare_if_dirty(plan, s)) != DAS_OK) return rc;
+    TileArgs A = tile_args(plan, 1, 1, 1, nullptr);
+    A.partial = plan->partial;
+    DAS_CU(launch_tile(A, MODE_COUNT, 0, DAS_STORE_F32, 1, 1, s));
+    DAS_CU(launch_reduce(plan->partial, n_tiles(plan->g), plan->scalar, s));
+    plan->launches += 2;
+    double v = 0;
+    DAS_CU(cudaMemcpyAsync(&v, plan->scalar, sizeof(double), cudaMemcpyDeviceToHost, s));
+    DAS_CU(cudaStreamSynchronize(s));
+    *count_host = (long long)llround(v);
+    return DAS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,244 @@
+// das_prep.cu -- per-plan preparation and channel-data relayout kernels.
+//
+//  * prepare: transmit delays (Sec. 2, Eq. 1 footnote) per (tile, transmit) as
+//    an integer base in samples plus a float32 rest per voxel, built in float64
+//    for the plan's current c.  The paper likewise keeps tau^tx precomputed per
+//    voxel while receive delays are computed in-kernel (Sec. 3.1).
+//  * scale: per (transmit, element) max |sample| for 16-bit storage (Sec. 3.3).
+//  * relayout: y[b][q][m][k] -> z[q][m][k][b] with the batch index innermost
+//    (Sec. 3.2, batch-inner layout), fused with the IQ pre-rotation by
+//    e^{i theta k} and the conversion to the storage type (Sec. 3.3).
+//  * reduce: deterministic sum of per-CTA partials.
+#include "das_internal.cuh"
+
+namespace das {
+
+// ---------------------------------------------------------------------------
+// prepare
+// ---------------------------------------------------------------------------
+
+__device__ inline double tx_path(int kind, double vx, double vy, double vz, double off, double t0x, double t0y,
+                                 double t0z, double px, double py, double pz) {
+    if (kind == 0) {
+        double dx = px - vx, dy = py - vy, dz = pz - vz;
+        return sqrt(dx * dx + dy * dy + dz * dz) - off;
+    }
+    if (kind == 1) return vx * (px - t0x) + vy * (py - t0y) + vz * (pz - t0z);
+    return 0.0;
+}
+
+// One CTA per tile, one thread per voxel lane.
+__global__ void __launch_bounds__(TILE_N) prepare_kernel(GridDesc g, int Q, const int *__restrict__ kind,
+                                                         const double *__restrict__ vec,
+                                                         const double *__restrict__ off, double t0x, double t0y,
+                                                         double t0z, double ad, int *__restrict__ tx_tb,
+                                                         float *__restrict__ tx_t) {
+    const long long tile = blockIdx.x;
+    const int tx = (int)(tile % g.tiles_x);
+    const int ty = (int)((tile / g.tiles_x) % g.tiles_y);
+    const int tz = (int)(tile / ((long long)g.tiles_x * g.tiles_y));
+    int lx, ly, lz;
+    lane_offset(threadIdx.x, lx, ly, lz);
+    double cx, cy, cz;
+    tile_centre(g, tx, ty, tz, cx, cy, cz);
+    const double px = g.ox + g.sx * (tx * TILE_X + lx);
+    const double py = g.oy + g.sy * (ty * TILE_Y + ly);
+    const double pz = g.oz + g.sz * (tz * TILE_Z + lz);
+    for (int q = 0; q < Q; ++q) {
+        const int kd = kind[q];
+        const double vx = vec[3 * q], vy = vec[3 * q + 1], vz = vec[3 * q + 2], o = off[q];
+        const double base = floor(ad * tx_path(kd, vx, vy, vz, o, t0x, t0y, t0z, cx, cy, cz));
+        const double t = ad * tx_path(kd, vx, vy, vz, o, t0x, t0y, t0z, px, py, pz) - base;
+        tx_t[(tile * Q + q) * TILE_N + threadIdx.x] = (float)t;
+        if (threadIdx.x == 0) tx_tb[tile * Q + q] = (int)base;
+    }
+}
+
+cudaError_t launch_prepare(const GridDesc &g, int Q, const int *kind, const double *vec, const double *off,
+                           const double *t0, double ad, int *tx_tb, float *tx_t, cudaStream_t s) {
+    const long long nt = n_tiles(g);
+    prepare_kernel<<<(unsigned)nt, TILE_N, 0, s>>>(g, Q, kind, vec, off, t0[0], t0[1], t0[2], ad, tx_tb, tx_t);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// storage conversion helpers
+// ---------------------------------------------------------------------------
+
+template <int ST> struct StoreT;
+template <> struct StoreT<ST_F32> { using c = float2; using r = float; };
+template <> struct StoreT<ST_F16> { using c = __half2; using r = __half; };
+template <> struct StoreT<ST_BF16> { using c = __nv_bfloat162; using r = __nv_bfloat16; };
+
+__device__ inline void put(float2 *p, float2 v) { *p = v; }
+__device__ inline void put(__half2 *p, float2 v) { *p = __floats2half2_rn(v.x, v.y); }
+__device__ inline void put(__nv_bfloat162 *p, float2 v) { *p = __floats2bfloat162_rn(v.x, v.y); }
+__device__ inline void put(float *p, float v) { *p = v; }
+__device__ inline void put(__half *p, float v) { *p = __float2half_rn(v); }
+__device__ inline void put(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+
+__device__ inline float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+
+// ---------------------------------------------------------------------------
+// scale: per (q, m) row set, the largest |component| over frames and samples
+// ---------------------------------------------------------------------------
+
+template <bool IQ>
+__global__ void __launch_bounds__(256) scale_kernel(const float *__restrict__ y, float *__restrict__ scale,
+                                                    float *__restrict__ inv_scale, int B, int QM, int K) {
+    const int qm = blockIdx.x;
+    const int comp = IQ ? 2 : 1;
+    float mx = 0.f;
+    for (int b = 0; b < B; ++b) {
+        const float *row = y + ((size_t)b * QM + qm) * (size_t)K * comp;
+        for (int i = threadIdx.x; i < K * comp; i += blockDim.x) mx = fmaxf(mx, fabsf(row[i]));
+    }
+    __shared__ float red[32];
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        mx = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (threadIdx.x == 0) {
+            const float s = (mx > 0.f && isfinite(mx)) ? mx : 1.f;
+            scale[qm] = s;
+            inv_scale[qm] = 1.f / s;
+        }
+    }
+}
+
+cudaError_t launch_scale(const void *y, float *scale, float *inv_scale, int iq, int store, int B, int QM, int K,
+                         cudaStream_t s) {
+    (void)store;
+    if (iq) scale_kernel<true><<<QM, 256, 0, s>>>((const float *)y, scale, inv_scale, B, QM, K);
+    else scale_kernel<false><<<QM, 256, 0, s>>>((const float *)y, scale, inv_scale, B, QM, K);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// relayout
+// ---------------------------------------------------------------------------
+
+// Batched: 32 frames x 32 samples per step through shared memory; reads are
+// contiguous along k, writes contiguous along b.  Frames B..Bs-1 are zero.
+template <bool IQ, int ST>
+__global__ void __launch_bounds__(256) relayout_kernel(const void *__restrict__ y_, void *__restrict__ z_,
+                                                       const float2 *__restrict__ rot,
+                                                       const float *__restrict__ inv_scale, int B, int Bs, int QM,
+                                                       int K) {
+    using OutC = typename StoreT<ST>::c;
+    using OutR = typename StoreT<ST>::r;
+    __shared__ float2 tile[32][33];
+    const int k0 = blockIdx.x * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int qm = blockIdx.y; qm < QM; qm += gridDim.y) {
+    const float s = inv_scale ? inv_scale[qm] : 1.f;
+    for (int bc = 0; bc < Bs; bc += 32) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int b = bc + ty + 8 * i, k = k0 + tx;
+            float2 v = make_float2(0.f, 0.f);
+            if (b < B && k < K) {
+                const size_t idx = ((size_t)b * QM + qm) * (size_t)K + k;
+                if (IQ) v = reinterpret_cast<const float2 *>(y_)[idx];
+                else v.x = reinterpret_cast<const float *>(y_)[idx];
+            }
+            tile[ty + 8 * i][tx] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int kl = ty + 8 * i, k = k0 + kl, b = bc + tx;
+            if (k < K && b < Bs) {
+                float2 v = tile[tx][kl];
+                const size_t o = ((size_t)qm * K + k) * (size_t)Bs + b;
+                if (IQ) {
+                    if (rot) v = cmul(v, rot[k]);
+                    v.x *= s;
+                    v.y *= s;
+                    put(reinterpret_cast<OutC *>(z_) + o, v);
+                } else {
+                    put(reinterpret_cast<OutR *>(z_) + o, v.x * s);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    }
+}
+
+// Single frame: the layouts coincide; rotate / scale / convert elementwise.
+template <bool IQ, int ST>
+__global__ void __launch_bounds__(256) convert1_kernel(const void *__restrict__ y_, void *__restrict__ z_,
+                                                       const float2 *__restrict__ rot,
+                                                       const float *__restrict__ inv_scale, int QM, int K) {
+    using OutC = typename StoreT<ST>::c;
+    using OutR = typename StoreT<ST>::r;
+    const size_t total = (size_t)QM * K;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(i % K);
+        const float s = inv_scale ? inv_scale[i / K] : 1.f;
+        if (IQ) {
+            float2 v = reinterpret_cast<const float2 *>(y_)[i];
+            if (rot) v = cmul(v, rot[k]);
+            v.x *= s;
+            v.y *= s;
+            put(reinterpret_cast<OutC *>(z_) + i, v);
+        } else {
+            put(reinterpret_cast<OutR *>(z_) + i, reinterpret_cast<const float *>(y_)[i] * s);
+        }
+    }
+}
+
+template <bool IQ, int ST>
+static void relayout_dispatch(const void *y, void *z, const float2 *rot, const float *inv_scale, int B, int Bs, int QM,
+                              int K, cudaStream_t s) {
+    if (Bs == 1) {
+        const size_t total = (size_t)QM * K;
+        const int blocks = (int)((total + 255) / 256 < 152 * 32 ? (total + 255) / 256 : 152 * 32);
+        convert1_kernel<IQ, ST><<<blocks, 256, 0, s>>>(y, z, rot, inv_scale, QM, K);
+    } else {
+        dim3 grid((K + 31) / 32, QM < 65535 ? QM : 65535);
+        relayout_kernel<IQ, ST><<<grid, 256, 0, s>>>(y, z, rot, inv_scale, B, Bs, QM, K);
+    }
+}
+
+cudaError_t launch_relayout(const void *y, void *z, const float2 *rot, const float *inv_scale, int iq, int store,
+                            int B, int Bs, int QM, int K, cudaStream_t s) {
+    if (iq) {
+        if (store == ST_F32) relayout_dispatch<true, ST_F32>(y, z, rot, inv_scale, B, Bs, QM, K, s);
+        else if (store == ST_F16) relayout_dispatch<true, ST_F16>(y, z, rot, inv_scale, B, Bs, QM, K, s);
+        else relayout_dispatch<true, ST_BF16>(y, z, rot, inv_scale, B, Bs, QM, K, s);
+    } else {
+        if (store == ST_F32) relayout_dispatch<false, ST_F32>(y, z, rot, inv_scale, B, Bs, QM, K, s);
+        else if (store == ST_F16) relayout_dispatch<false, ST_F16>(y, z, rot, inv_scale, B, Bs, QM, K, s);
+        else relayout_dispatch<false, ST_BF16>(y, z, rot, inv_scale, B, Bs, QM, K, s);
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// reduce: one CTA, fixed order, float64
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(1024) reduce_kernel(const double *__restrict__ partial, long long n,
+                                                      double *__restrict__ out) {
+    double acc = 0.0;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) acc += partial[i];
+    __shared__ double red[1024];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0];
+}
+
+cudaError_t launch_reduce(const double *partial, long long n, double *out, cudaStream_t s) {
+    reduce_kernel<<<1, 1024, 0, s>>>(partial, n, out);
+    return cudaGetLastError();
+}
+
+}  // namespace das

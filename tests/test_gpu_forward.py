@@ -1,0 +1,172 @@
+"""GPU parity of the forward pass against the FP64 oracle (through the C-ABI).
+
+Floating-point bar: relative L2 error <= 1e-5 for float32 storage (the
+accuracy asked of the plain float32 form), <= 2e-3 for 16-bit storage.
+Integer decisions (which terms contribute) are compared exactly through the
+term count, on scenes whose aperture tests have no near-ties.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2606_13259_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+MM = 1e-3
+TOL_F32 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def das():
+    import __graft_entry__ as G
+
+    G.build()
+    import paper_2606_13259_gb300 as P
+
+    torch.cuda.set_device(0)
+    return P
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def run_forward(das, scene, y, storage="f32", fb=0):
+    plan = das.Plan.from_scene(scene, storage=storage, max_batch=y.shape[0])
+    if fb:
+        plan.set_tuning(frames_per_thread=fb)
+    x = plan.forward(y.cuda()).cpu().numpy().reshape(y.shape[0], -1)
+    plan.close()
+    return x
+
+
+def test_small_rf_matches_oracle(das, oracle):
+    """32^3 voxels, 256 elements, 1 diverging wave, RF f32, simulated speckle + points + noise."""
+    sc = S.scene_small()
+    y = S.frames(sc, 1, seed=1, n_speckle=2000, points=S.SMALL_POINTS, noise_db=30.0)
+    x = run_forward(das, sc, y)
+    ref = oracle.forward(sc, y.numpy())
+    assert rel_l2(x, ref) <= TOL_F32
+    img = np.abs(x[0]).reshape(sc.nz, sc.ny, sc.nx)
+    for ix, iy, iz in S.SMALL_POINTS:
+        sub = img[iz - 2:iz + 3, iy - 2:iy + 3, ix - 2:ix + 3]
+        assert np.unravel_index(np.argmax(sub), sub.shape) == (2, 2, 2)
+
+
+def test_small_iq_matches_oracle(das, oracle):
+    sc = S.scene_small_iq()
+    y = S.frames(sc, 1, seed=1, n_speckle=2000, points=S.SMALL_POINTS, noise_db=30.0)
+    x = run_forward(das, sc, y)
+    ref = oracle.forward(sc, y.numpy())
+    assert rel_l2(x, ref) <= TOL_F32
+
+
+RAGGED = [
+    # (iq, grid, elems, n_tx, f_number, K, kinds)
+    (True, (13, 7, 9), (5, 3), 3, 1.0, 96, (S.TX_DIVERGING, S.TX_PLANE, S.TX_NONE)),
+    (False, (9, 5, 6), (4, 4), 2, 0.0, 80, (S.TX_DIVERGING, S.TX_DIVERGING)),
+    (True, (8, 4, 4), (3, 2), 2, 0.7, 56, (S.TX_PLANE, S.TX_DIVERGING)),
+    (True, (17, 11, 5), (6, 5), 4, 1.3, 40, (S.TX_DIVERGING,) * 4),  # short K: many terms out of range
+]
+
+
+def ragged_scene(iq, grid, elems, n_tx, fnum, K, kinds):
+    sc = S.scene_tiny(iq=iq, n=grid, elems=elems, n_tx=n_tx, f_number=fnum, K=K)
+    vec = sc.tx_vec.copy()
+    for q, k in enumerate(kinds):
+        if k == S.TX_PLANE:
+            a = 0.2 * (q - 1)
+            vec[q] = [np.sin(a), 0.0, np.cos(a)]
+    return sc.with_(tx_kind=np.array(kinds, np.int32), tx_vec=vec)
+
+
+@pytest.mark.parametrize("case", range(len(RAGGED)))
+@pytest.mark.parametrize("B", [1, 3, 7])
+def test_ragged_tiles_transmit_kinds_and_batches(das, oracle, case, B):
+    sc = ragged_scene(*RAGGED[case])
+    y = S.random_channels(sc, B, seed=10 + case)
+    x = run_forward(das, sc, y)
+    ref = oracle.forward(sc, y.numpy())
+    assert rel_l2(x, ref) <= TOL_F32
+
+
+@pytest.mark.parametrize("fb", [1, 2, 4, 8, 12, 16, 20])
+def test_frames_per_thread_variants(das, oracle, fb):
+    """Every compiled frames-per-thread width gives the same image (padding of
+    the last frame chunk included)."""
+    sc = ragged_scene(*RAGGED[0])
+    B = 21
+    y = S.random_channels(sc, B, seed=5)
+    x = run_forward(das, sc, y, fb=fb)
+    ref = oracle.forward(sc, y.numpy())
+    assert rel_l2(x, ref) <= TOL_F32
+
+
+def test_transmit_weights(das, oracle):
+    sc = ragged_scene(*RAGGED[0])
+    rng = np.random.default_rng(2)
+    sc = sc.with_(w_tx=rng.random((sc.Q, sc.N)).astype(np.float32))
+    y = S.random_channels(sc, 2, seed=3)
+    assert rel_l2(run_forward(das, sc, y), oracle.forward(sc, y.numpy())) <= TOL_F32
+
+
+def test_iq_without_demodulation_and_no_time_offset(das, oracle):
+    sc = ragged_scene(*RAGGED[2]).with_(f_demod=0.0, t0_offset=False, K=128)
+    y = S.random_channels(sc, 2, seed=4)
+    assert rel_l2(run_forward(das, sc, y), oracle.forward(sc, y.numpy())) <= TOL_F32
+
+
+@pytest.mark.parametrize("name", ["small", "small_iq", "ragged0", "ragged3"])
+def test_term_count_is_exact(das, oracle, name):
+    sc = {"small": S.scene_small, "small_iq": S.scene_small_iq,
+          "ragged0": lambda: ragged_scene(*RAGGED[0]), "ragged3": lambda: ragged_scene(*RAGGED[3])}[name]()
+    assert oracle.count_near_ties(sc, 1e-5) == 0
+    plan = das.Plan.from_scene(sc)
+    assert plan.count_active() == oracle.count_active(sc)
+    plan.close()
+
+
+@pytest.mark.parametrize("storage,tol", [("f16", 2e-3), ("bf16", 2e-2)])
+@pytest.mark.parametrize("iq", [False, True])
+def test_16bit_storage(das, oracle, storage, tol, iq):
+    """16-bit storage with a float32 scale per (transmit, element), float32 sums."""
+    sc = S.scene_small_iq() if iq else S.scene_small()
+    y = S.frames(sc, 2, seed=1, n_speckle=2000, points=S.SMALL_POINTS, noise_db=30.0)
+    x = run_forward(das, sc, y, storage=storage)
+    ref = oracle.forward(sc, y.numpy())
+    err = rel_l2(x, ref)
+    print(f"{storage} iq={iq}: relative L2 {err:.3e}")
+    assert err <= tol
+
+
+def test_paper_scale_sampled(das, oracle):
+    """128^3 voxels x 1024 elements x 16 transmits, 20 IQ frames, in the launch
+    configuration the benchmark times; compared on 96 sampled voxels."""
+    sc = S.scene_paper()
+    B = 20
+    y = S.frames(sc, B, seed=2, n_speckle=20000, points=S.paper_points(sc), device="cuda")
+    plan = das.Plan.from_scene(sc, max_batch=B)
+    x = plan.forward(y).reshape(B, -1)
+    rng = np.random.default_rng(0)
+    vox = np.sort(rng.choice(sc.N, 96, replace=False))
+    pts = [sc.voxel_index(*p) for p in S.paper_points(sc)]
+    vox = np.concatenate([vox, pts])
+    got = x[:, torch.as_tensor(vox, device="cuda")].cpu().numpy()
+    ref = oracle.forward(sc, y.cpu().numpy(), voxels=vox)
+    err = rel_l2(got, ref)
+    print(f"paper scale: relative L2 {err:.3e} on {vox.size} voxels x {B} frames")
+    assert err <= TOL_F32
+    plan.close()
+
+
+def test_invalid_arguments_raise(das):
+    sc = S.scene_tiny()
+    plan = das.Plan.from_scene(sc, max_batch=2)
+    y = S.random_channels(sc, 3, seed=0).cuda()
+    with pytest.raises(ValueError):
+        plan.forward(y)  # batch above max_batch
+    with pytest.raises(TypeError):
+        plan.forward(y[:1].real.contiguous())
+    plan.close()
+    with pytest.raises(das.DASError):
+        das.Plan.from_scene(sc.with_(c=-1.0))
