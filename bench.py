@@ -39,6 +39,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--frames", type=int, default=20)
+    ap.add_argument("--K", type=int, default=2048, help="samples per channel (all delays lie below 400)")
     ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -132,10 +133,10 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def make_inputs(frames: int, rank: int, device):
+def make_inputs(frames: int, rank: int, device, K: int = 2048):
     from paper_2606_13259_gb300 import synth as S
 
-    sc = S.scene_paper()
+    sc = S.scene_paper(K)
     y = S.frames(sc, frames, seed=2 + 1000 * rank, n_speckle=20000, points=S.paper_points(sc), device=device)
     return sc, y
 
@@ -172,7 +173,7 @@ def run_reference(args):
     if rank != 0:
         return
     dev = "cuda" if torch.cuda.is_available() else "cpu"
-    sc, y = make_inputs(args.frames, 0, dev)
+    sc, y = make_inputs(args.frames, 0, dev, args.K)
     y_cpu = y.cpu().numpy()
     del y
     from oracle import oracle as O
@@ -232,7 +233,7 @@ def main():
         dist.barrier()
     dev = torch.device("cuda", torch.cuda.current_device())
 
-    sc, y = make_inputs(args.frames, rank, dev)
+    sc, y = make_inputs(args.frames, rank, dev, args.K)
     F = args.frames
     plan = Plan.from_scene(sc, storage=args.storage, max_batch=F)
     out = torch.empty((F,) + plan.shape, dtype=torch.complex64, device=dev)
@@ -313,7 +314,7 @@ def main():
         "data": "synthetic (seeded speckle + 10 point targets, time-domain simulator)",
         "config": {"workload": sc.name, "frames_per_step": F, "voxels": sc.N, "elements": sc.M,
                    "transmits": sc.Q, "samples": sc.K, "storage": args.storage,
-                   "l2": "inputs 5.4 GB > 129 MB L2, no flush", "per_rank_frames": F},
+                   "l2": f"inputs {y.numel() * 8 / 1e9:.1f} GB > 129 MB L2, no flush", "per_rank_frames": F},
         "accumulations_per_s": world * F * sc.N * sc.M * sc.Q / (ms * 1e-3),
         "contributing_terms_per_volume": active,
         "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,

@@ -179,7 +179,7 @@ def scenes_batched() -> list[Scene]:
 
 def scene_tiny(iq: bool = True, n: tuple = (3, 3, 3), elems: tuple = (2, 2), n_tx: int = 2,
                K: int = 64, f_number: float = 0.0) -> Scene:
-    """A few voxels and elements for brute-force checks (fs 30 MHz, 1 mm voxel pitch at depth 1 mm)."""
+    """A few voxels and elements for brute-force checks (fs 30 MHz, 0.1 mm voxels from 1 mm depth)."""
     pos, nrm = matrix_array(elems[0], elems[1], 0.3 * MM)
     src = [[0.4 * MM * (q - (n_tx - 1) / 2.0), 0.0, -5 * MM] for q in range(n_tx)]
     kind, vec = _diverging(src)
@@ -218,33 +218,37 @@ def phantom(scene: Scene, n_speckle: int, points: Sequence[tuple], seed: int,
     return pos, amp
 
 
-def arrival_times(scene: Scene, pos, c: float, xp):
+def arrival_times(scene: Scene, pos, c: float):
     """Two-way travel time (seconds) from transmit to reflector to element,
-    [Q][M][L].  The clock starts when the transmitted wave passes t0_ref
-    (for a diverging wave: ||s - v|| - ||v - t0_ref||); plane waves start at
-    t0_ref; without a transmit only the return path counts."""
+    [Q][M][L], for reflectors pos (L, 3) (a torch tensor).  The clock starts
+    when the transmitted wave passes t0_ref (for a diverging wave:
+    ||s - v|| - ||v - t0_ref||); plane waves start at t0_ref; without a
+    transmit only the return path counts."""
+    import torch
+
     s = pos                                      # (L, 3)
-    r = xp.asarray(scene.elem_pos, dtype=s.dtype)
-    back = xp.sqrt(((s[None, :, :] - r[:, None, :]) ** 2).sum(-1))     # (M, L)
-    t0 = xp.asarray(np.asarray(scene.t0_ref, dtype=np.float64), dtype=s.dtype)
+    as_t = lambda a: torch.as_tensor(np.asarray(a, dtype=np.float64), dtype=s.dtype, device=s.device)
+    r = as_t(scene.elem_pos)
+    back = torch.sqrt(((s[None, :, :] - r[:, None, :]) ** 2).sum(-1))     # (M, L)
+    t0 = as_t(scene.t0_ref)
     outs = []
     for q in range(scene.Q):
-        v = xp.asarray(scene.tx_vec[q], dtype=s.dtype)
+        v = as_t(scene.tx_vec[q])
         kind = int(scene.tx_kind[q])
         if kind == TX_DIVERGING:
-            out_path = xp.sqrt(((s - v) ** 2).sum(-1))
+            out_path = torch.sqrt(((s - v) ** 2).sum(-1))
             if scene.t0_offset:
                 out_path = out_path - float(np.linalg.norm(scene.tx_vec[q] - np.asarray(scene.t0_ref)))
         elif kind == TX_PLANE:
             out_path = ((s - t0) * v).sum(-1)
         else:
-            out_path = xp.zeros(s.shape[0], dtype=s.dtype)
+            out_path = torch.zeros(s.shape[0], dtype=s.dtype, device=s.device)
         outs.append((out_path[None, :] + back) / c)
-    return xp.stack(outs)                        # (Q, M, L)
+    return torch.stack(outs)                     # (Q, M, L)
 
 
 def simulate(scene: Scene, pos: np.ndarray, amp: np.ndarray, *, c: Optional[float] = None,
-             noise_db: Optional[float] = None, seed: int = 0, device="cpu", chunk: int = 256):
+             noise_db: Optional[float] = None, seed: int = 0, device="cpu", chunk: int = 512):
     """Channel data of one acquisition, torch tensor [Q][M][K] (complex64 for IQ,
     float32 for RF) on `device`.
 
@@ -269,7 +273,7 @@ def simulate(scene: Scene, pos: np.ndarray, amp: np.ndarray, *, c: Optional[floa
     pos_t = torch.as_tensor(pos, dtype=torch.float64, device=dev)
     amp_t = torch.as_tensor(amp, dtype=torch.float64, device=dev)
     for s0 in range(0, pos_t.shape[0], chunk):
-        tau = arrival_times(scene, pos_t[s0:s0 + chunk], c, torch)              # (Q, M, L) s
+        tau = arrival_times(scene, pos_t[s0:s0 + chunk], c)                     # (Q, M, L) s
         ts = tau * scene.fs
         kk = torch.floor(ts).unsqueeze(-1) + taps                               # (Q, M, L, T)
         valid = (kk >= 0) & (kk <= K - 1)
