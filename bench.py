@@ -133,11 +133,27 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def rank_seed(rank: int) -> int:
+    """Each rank beamforms its own independent frames (weak scaling)."""
+    return 2 + 100000 * rank
+
+
+def max_over_ranks(values, dist, device):
+    """Element-wise maximum of per-rank timings (the slowest rank sets the step time)."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+
+    t = torch.tensor([float(v) for v in values], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
 def make_inputs(frames: int, rank: int, device, K: int = 2048):
     from paper_2606_13259_gb300 import synth as S
 
     sc = S.scene_paper(K)
-    y = S.frames(sc, frames, seed=2 + 1000 * rank, n_speckle=20000, points=S.paper_points(sc), device=device)
+    y = S.frames(sc, frames, seed=rank_seed(rank), n_speckle=20000, points=S.paper_points(sc), device=device)
     return sc, y
 
 
@@ -265,10 +281,7 @@ def main():
     kern_ms_total, kern_n = plan.timing()
     kern_ms = kern_ms_total / max(kern_n, 1)
     launches = plan.info()["kernel_launches"] - launches0
-    if dist:
-        t = torch.tensor([ms, kern_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, kern_ms = float(t[0]), float(t[1])
+    ms, kern_ms = max_over_ranks([ms, kern_ms], dist, dev)
 
     # end to end through the C-ABI with host buffers (copies inside the timed region)
     e2e = None
@@ -284,10 +297,7 @@ def main():
         for _ in range(n_e2e):
             plan.forward_host(y_host, x_host)
         dt = (time.perf_counter() - t0) / n_e2e
-        if dist:
-            t = torch.tensor([dt], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t[0])
+        (dt,) = max_over_ranks([dt], dist, dev)
         e2e = {"value": world * F / dt, "unit": "volumes/s", "h2d_bytes_per_step": y_host.numel() * 8,
                "d2h_bytes_per_step": x_host.numel() * 8, "ms_per_step": dt * 1e3}
         del y_host, x_host
