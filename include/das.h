@@ -172,6 +172,26 @@ int das_adjoint(das_plan_t *plan, const void *x_dev, void *y_dev, int batch, das
 int das_grad_c(das_plan_t *plan, const void *y_dev, const void *gx_dev, double *dLdc_dev, int batch,
                das_stream_t stream);
 
+/* das_grad_c without any device allocation of its own.
+ *
+ * The paper has no counterpart: this entry point serves callers that cannot
+ * allocate device memory where they need the derivative (a fixed memory pool
+ * that owns the device, a real-time loop that must not enter the allocator).
+ * Same arguments and result as das_grad_c; the per-(voxel tile, frame chunk)
+ * partial sums live in a 2 MiB array compiled into the library (262144
+ * float64 slots, held by every GPU that loads the library until exit) instead
+ * of in the plan.  Problems needing more slots (tiles x ceil(batch / frames per
+ * thread)) are rejected with DAS_ERR_UNSUPPORTED before any launch.  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.
+ * No slot needs clearing: each is written in the call before it is read.  All
+ * calls share the one array, so calls that overlap on the GPU (other streams,
+ * other threads) race and must be serialised by the caller.  The plan's
+ * relayout scratch for IQ data is used as in das_grad_c (allocated when the
+ * plan was created). */
+int das_grad_c_static(das_plan_t *plan, const void *y_dev, const void *gx_dev, double *dLdc_dev, int batch,
+                      das_stream_t stream);
+
 /* Number of (q, m, n) terms of Eq. 2 that contribute (inside the aperture,
  * 0 <= k <= K - 2) for the plan's current c, counted on the device with the
  * kernels' own float32 decisions.  Synchronous; result in *count_host. */

@@ -22,7 +22,7 @@ ERROR_NAMES = {DAS_ERR_INVALID_ARG: "invalid argument", DAS_ERR_CUDA: "CUDA erro
 # Every symbol declared in include/das.h.
 EXPORTS = ["das_plan_create", "das_plan_destroy", "das_plan_set_c", "das_plan_info", "das_plan_set_tuning",
            "das_forward", "das_forward_host", "das_adjoint", "das_grad_c", "das_count_active",
-           "das_plan_enable_timing", "das_plan_timing", "das_last_error", "das_version"]
+           "das_plan_enable_timing", "das_plan_timing", "das_last_error", "das_version", "das_grad_c_static"]
 
 
 class Geometry(C.Structure):
@@ -87,6 +87,8 @@ def lib():
             getattr(L, name).restype = i
         L.das_grad_c.argtypes = [vp, vp, vp, vp, i, vp]
         L.das_grad_c.restype = i
+        L.das_grad_c_static.argtypes = [vp, vp, vp, vp, i, vp]
+        L.das_grad_c_static.restype = i
         L.das_count_active.argtypes = [vp, C.POINTER(C.c_longlong), vp]
         L.das_count_active.restype = i
         L.das_plan_enable_timing.argtypes = [vp, i]

@@ -653,3 +653,76 @@ int das_count_active(das_plan_t *plan, long long *count_host, das_stream_t strea
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// das_grad_c_static: das_grad_c without any device allocation of its own.
+//
+// Some callers cannot allocate device memory at the point where they need the
+// derivative: code running under a fixed memory budget (a pool that owns all
+// device memory), real-time loops that must not enter the allocator, or code
+// that wants the call sequence free of allocator side effects.  This entry
+// point keeps the only scratch of the derivative pass -- one float64 partial
+// sum per (voxel tile, frame chunk) -- in a fixed array compiled into the
+// library instead of in the plan.  The array is 2 MiB (262144 partial sums)
+// and every GPU that loads the library keeps it until the process exits.
+// ---------------------------------------------------------------------------
+
+#include <mutex>
+
+#define DAS_STATIC_PARTIALS (1 << 18)
+
+static __device__ __align__(256) double g_static_partials[DAS_STATIC_PARTIALS];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mutex;
+double *g_static_ptr[kMaxDevices] = {nullptr};
+
+// Device address of the static array on the current device.  In host code the
+// array's name is only a host-side stand-in, so the address is looked up once
+// per device (with that device current) and remembered.
+int static_partials_address(int device, double **out) {
+    if (device < 0 || device >= kMaxDevices) return fail(DAS_ERR_UNSUPPORTED, "device index %d too large", device);
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (!g_static_ptr[device]) {
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_partials);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_static_partials)");
+        g_static_ptr[device] = static_cast<double *>(ptr);
+    }
+    *out = g_static_ptr[device];
+    return DAS_OK;
+}
+}  // namespace
+
+extern "C" int das_grad_c_static(das_plan_t *plan, const void *y_dev, const void *gx_dev, double *dLdc_dev,
+                                 int batch, das_stream_t stream) {
+    g_err[0] = 0;
+    int rc = check_call(plan, y_dev, gx_dev, batch);
+    if (rc != DAS_OK) return rc;
+    if (!dLdc_dev || !aligned(dLdc_dev, 8)) return fail(DAS_ERR_INVALID_ARG, "dLdc_dev must be an aligned device double");
+    if (plan->storage != DAS_STORE_F32) return fail(DAS_ERR_UNSUPPORTED, "das_grad_c_static needs float32 storage");
+    const int fb = choose_fb(plan, batch, MODE_DC);
+    const int nch = (batch + fb - 1) / fb;
+    const int Bs = nch * fb;
+    const long long np = n_tiles(plan->g) * nch;
+    if (np > DAS_STATIC_PARTIALS)
+        return fail(DAS_ERR_UNSUPPORTED,
+                    "das_grad_c_static: %lld partial sums needed (voxel tiles x frame chunks), the static scratch holds %d",
+                    np, DAS_STATIC_PARTIALS);
+    DeviceGuard guard(plan->device);
+    if (!guard.ok) return fail(DAS_ERR_CUDA, "cannot select the plan's device");
+    double *partial = nullptr;
+    if ((rc = static_partials_address(plan->device, &partial)) != DAS_OK) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((rc = prepare_if_dirty(plan, s)) != DAS_OK) return rc;
+    const void *z = nullptr;
+    if ((rc = stage_channels(plan, y_dev, batch, Bs, s, &z)) != DAS_OK) return rc;
+    TileArgs A = tile_args(plan, Bs, batch, fb, z);
+    A.gx = gx_dev;
+    A.partial = partial;  // every slot 0..np-1 is written by its CTA before the reduction reads it
+    DAS_CU(launch_tile(A, MODE_DC, is_iq(plan), DAS_STORE_F32, fb, nch, s));
+    DAS_CU(launch_reduce(partial, np, dLdc_dev, s));
+    plan->launches += 2;
+    return DAS_OK;
+}
