@@ -265,27 +265,35 @@ def simulate(scene: Scene, pos: np.ndarray, amp: np.ndarray, *, c: Optional[floa
     c = scene.c if c is None else c
     dev = torch.device(device)
     K, Q, M = scene.K, scene.Q, scene.M
-    sigma = (2.0 / scene.fc) / (2.0 * math.sqrt(2.0 * math.log(2.0)))
-    half = int(math.ceil(4.0 * sigma * scene.fs)) + 1
-    taps = torch.arange(-half, half + 2, device=dev, dtype=torch.float64)        # (T,)
+    sigma_s = (2.0 / scene.fc) / (2.0 * math.sqrt(2.0 * math.log(2.0))) * scene.fs   # envelope width, samples
+    half = int(math.ceil(4.0 * sigma_s)) + 1
+    taps = torch.arange(-half, half + 2, device=dev, dtype=torch.float32)        # (T,)
     out = torch.zeros(Q * M * K, 2, device=dev, dtype=torch.float32)
     row = (torch.arange(Q * M, device=dev, dtype=torch.int64) * K).view(Q, M, 1, 1)
     pos_t = torch.as_tensor(pos, dtype=torch.float64, device=dev)
-    amp_t = torch.as_tensor(amp, dtype=torch.float64, device=dev)
+    amp_t = torch.as_tensor(amp, dtype=torch.float32, device=dev)
+    w_env = 1.0 / (2.0 * sigma_s * sigma_s)
+    w_bb = 2.0 * math.pi * (scene.fc - scene.f_demod) / scene.fs                  # baseband rad/sample
     for s0 in range(0, pos_t.shape[0], chunk):
-        tau = arrival_times(scene, pos_t[s0:s0 + chunk], c)                     # (Q, M, L) s
+        tau = arrival_times(scene, pos_t[s0:s0 + chunk], c)                     # (Q, M, L) s, float64
         ts = tau * scene.fs
-        kk = torch.floor(ts).unsqueeze(-1) + taps                               # (Q, M, L, T)
+        k0 = torch.floor(ts)
+        frac = (ts - k0).to(torch.float32).unsqueeze(-1)                         # (Q, M, L, 1)
+        dts = taps - frac                                                        # t - tau, samples
+        env = amp_t[s0:s0 + chunk].view(1, 1, -1, 1) * torch.exp(-dts * dts * w_env)
+        kk = k0.to(torch.int64).unsqueeze(-1) + taps.to(torch.int64)
         valid = (kk >= 0) & (kk <= K - 1)
-        dt = kk / scene.fs - tau.unsqueeze(-1)                                  # t - tau
-        env = amp_t[s0:s0 + chunk].view(1, 1, -1, 1) * torch.exp(-dt * dt / (2 * sigma * sigma))
         if scene.iq:
-            ph = 2 * math.pi * (scene.fc - scene.f_demod) * dt - 2 * math.pi * scene.f_demod * tau.unsqueeze(-1)
+            # exp(-i 2 pi f_d tau) reduced to one turn in float64, then float32
+            turns = tau * scene.f_demod
+            carrier = (2.0 * math.pi * (turns - torch.floor(turns))).to(torch.float32).unsqueeze(-1)
+            ph = w_bb * dts - carrier
             vals = torch.stack([env * torch.cos(ph), env * torch.sin(ph)], -1)
         else:
-            vals = torch.stack([env * torch.cos(2 * math.pi * scene.fc * dt), torch.zeros_like(env)], -1)
-        idx = (row + kk.clamp(0, K - 1).to(torch.int64)).reshape(-1)
-        vals = (vals * valid.unsqueeze(-1)).reshape(-1, 2).to(torch.float32)
+            ph = (2.0 * math.pi * scene.fc / scene.fs) * dts
+            vals = torch.stack([env * torch.cos(ph), torch.zeros_like(env)], -1)
+        idx = (row + kk.clamp(0, K - 1)).reshape(-1)
+        vals = (vals * valid.unsqueeze(-1)).reshape(-1, 2)
         out.index_add_(0, idx, vals)
     if noise_db is not None:
         rng = np.random.Generator(np.random.PCG64(seed + 7919))
