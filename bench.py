@@ -44,6 +44,8 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-staging", action="store_true", help="read sample rows from global memory (no TMA windows)")
+    ap.add_argument("--fb", type=int, default=0, help="frames per thread (0: automatic)")
     return ap.parse_args()
 
 
@@ -57,7 +59,7 @@ def measured_peaks():
 
 def kernel_source_hash() -> str:
     h = hashlib.sha1()
-    for f in ("das_tile.cuh", "das_tile_f32.cu", "das_internal.cuh"):
+    for f in ("das_tile.cuh", "das_tile_tma.cuh", "das_tile_f32.cu", "das_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2606_13259_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
@@ -252,6 +254,8 @@ def main():
     sc, y = make_inputs(args.frames, rank, dev, args.K)
     F = args.frames
     plan = Plan.from_scene(sc, storage=args.storage, max_batch=F)
+    if args.no_staging or args.fb:
+        plan.set_tuning(frames_per_thread=args.fb, staging=not args.no_staging)
     out = torch.empty((F,) + plan.shape, dtype=torch.complex64, device=dev)
     active = plan.count_active()
 
@@ -278,6 +282,7 @@ def main():
         dist.barrier()
     clocks = sampler.stop() if sampler else None
     ms = e0.elapsed_time(e1) / args.steps
+    plan.check()
     kern_ms_total, kern_n = plan.timing()
     kern_ms = kern_ms_total / max(kern_n, 1)
     launches = plan.info()["kernel_launches"] - launches0
@@ -324,7 +329,8 @@ def main():
         "data": "synthetic (seeded speckle + 10 point targets, time-domain simulator)",
         "config": {"workload": sc.name, "frames_per_step": F, "voxels": sc.N, "elements": sc.M,
                    "transmits": sc.Q, "samples": sc.K, "storage": args.storage,
-                   "l2": f"inputs {y.numel() * 8 / 1e9:.1f} GB > 129 MB L2, no flush", "per_rank_frames": F},
+                   "l2": f"inputs {y.numel() * 8 / 1e9:.1f} GB > 129 MB L2, no flush", "per_rank_frames": F,
+                   "staging": not args.no_staging, "frames_per_thread": args.fb or "auto"},
         "accumulations_per_s": world * F * sc.N * sc.M * sc.Q / (ms * 1e-3),
         "contributing_terms_per_volume": active,
         "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,

@@ -124,6 +124,8 @@ typedef struct {
 typedef struct {
     int frames_per_thread; /* frames accumulated per thread in the forward kernel (0: automatic) */
     int ctas_per_sm;       /* occupancy hint for persistent launches (0: automatic) */
+    int no_staging;        /* 1: read sample rows straight from global memory instead of staging
+                              each (element, transmit) window in shared memory with bulk copies */
 } das_tuning_t;
 
 /* Build a plan (Sec. 2 problem statement: grid, receivers, observations, c).
@@ -196,6 +198,11 @@ int das_grad_c_static(das_plan_t *plan, const void *y_dev, const void *gx_dev, d
  * 0 <= k <= K - 2) for the plan's current c, counted on the device with the
  * kernels' own float32 decisions.  Synchronous; result in *count_host. */
 int das_count_active(das_plan_t *plan, long long *count_host, das_stream_t stream);
+
+/* Waits for the stream and reports kernel-side failures recorded since the
+ * last check: DAS_ERR_TIMEOUT when a kernel gave up waiting for a staged copy
+ * (it then left its outputs incomplete).  Clears the record. */
+int das_plan_check(das_plan_t *plan, das_stream_t stream);
 
 /* Kernel timing for benchmarks.  With capacity > 0 the plan records a CUDA
  * event pair around the delay-and-sum kernel of each following das_forward

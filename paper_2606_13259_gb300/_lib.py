@@ -22,7 +22,8 @@ ERROR_NAMES = {DAS_ERR_INVALID_ARG: "invalid argument", DAS_ERR_CUDA: "CUDA erro
 # Every symbol declared in include/das.h.
 EXPORTS = ["das_plan_create", "das_plan_destroy", "das_plan_set_c", "das_plan_info", "das_plan_set_tuning",
            "das_forward", "das_forward_host", "das_adjoint", "das_grad_c", "das_count_active",
-           "das_plan_enable_timing", "das_plan_timing", "das_last_error", "das_version", "das_grad_c_static"]
+           "das_plan_enable_timing", "das_plan_timing", "das_last_error", "das_version", "das_grad_c_static",
+           "das_plan_check"]
 
 
 class Geometry(C.Structure):
@@ -51,7 +52,7 @@ class PlanInfo(C.Structure):
 
 
 class Tuning(C.Structure):
-    _fields_ = [("frames_per_thread", C.c_int), ("ctas_per_sm", C.c_int)]
+    _fields_ = [("frames_per_thread", C.c_int), ("ctas_per_sm", C.c_int), ("no_staging", C.c_int)]
 
 
 class DASError(RuntimeError):
@@ -91,6 +92,8 @@ def lib():
         L.das_grad_c_static.restype = i
         L.das_count_active.argtypes = [vp, C.POINTER(C.c_longlong), vp]
         L.das_count_active.restype = i
+        L.das_plan_check.argtypes = [vp, vp]
+        L.das_plan_check.restype = i
         L.das_plan_enable_timing.argtypes = [vp, i]
         L.das_plan_enable_timing.restype = i
         L.das_plan_timing.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int)]

@@ -49,6 +49,8 @@ struct das_plan {
     double *tx_off = nullptr;
     int *tx_tb = nullptr;
     float *tx_t = nullptr;
+    float *tx_tmin = nullptr;
+    int *err = nullptr;
     float *w_tx = nullptr;
     float2 *rot = nullptr;
     float *scale = nullptr;
@@ -61,7 +63,7 @@ struct das_plan {
     void *stage_y = nullptr;
     void *stage_x = nullptr;
     bool dirty = true;
-    das_tuning_t tuning{0, 0};
+    das_tuning_t tuning{0, 0, 0};
     size_t bytes = 0;
     long long launches = 0;
     std::vector<cudaEvent_t> ev_start, ev_stop;
@@ -170,7 +172,8 @@ int ensure_scratch(das_plan *p) {
 
 int prepare_if_dirty(das_plan *p, cudaStream_t s) {
     if (!p->dirty) return DAS_OK;
-    DAS_CU(launch_prepare(p->g, p->Q, p->tx_kind, p->tx_vec, p->tx_off, p->t0, p->fs / p->c, p->tx_tb, p->tx_t, s));
+    DAS_CU(launch_prepare(p->g, p->Q, p->tx_kind, p->tx_vec, p->tx_off, p->t0, p->fs / p->c, p->tx_tb, p->tx_t,
+                          p->tx_tmin, s));
     p->launches += 1;
     p->dirty = false;
     return DAS_OK;
@@ -197,16 +200,20 @@ void fill_common(const das_plan *p, float &a, double &ad, float &theta, float &h
     rad = (float)(sqrt(rx * rx + ry * ry + rz * rz) * (1.0 + 1e-4) + 1e-9);
 }
 
-TileArgs tile_args(const das_plan *p, int Bs, int B, int fb, const void *z) {
+TileArgs tile_args(const das_plan *p, int B, int fb, const void *z) {
     TileArgs A{};
     A.g = p->g;
     A.M = p->M;
     A.Q = p->Q;
     A.K = p->K;
-    A.Bs = Bs;
     A.B = B;
     A.fb = fb;
     fill_common(p, A.a, A.ad, A.theta, A.hr, A.hi, A.thr, A.tile_radius);
+    const double aR = (p->fs / p->c) * (double)A.tile_radius;
+    A.umax = p->tuning.no_staging ? 0 : window_rows(aR);
+    A.win_lo = (float)(aR + 1e-3);
+    A.tx_tmin = p->tx_tmin;
+    A.err = p->err;
     A.inv_c = 1.0 / p->c;
     A.elem_pos = p->elem_pos;
     A.elem_nrm = p->elem_nrm;
@@ -222,7 +229,8 @@ bool aligned(const void *ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
 
 // Relayout of the public channel data into the plan scratch (or the data
 // itself when the layouts coincide).  Returns the pointer the kernels read.
-int stage_channels(das_plan *p, const void *y, int B, int Bs, cudaStream_t s, const void **z_out) {
+int stage_channels(das_plan *p, const void *y, int B, int fb, int nch, cudaStream_t s, const void **z_out) {
+    const int Bs = fb * nch;
     const bool iq = is_iq(p);
     const int QM = p->Q * p->M;
     if (p->storage != DAS_STORE_F32) {
@@ -236,7 +244,7 @@ int stage_channels(das_plan *p, const void *y, int B, int Bs, cudaStream_t s, co
     const size_t need = (size_t)QM * p->K * (size_t)Bs * sample_bytes_store(p);
     if (need > p->z_bytes) return fail(DAS_ERR_INVALID_ARG, "batch needs %zu bytes of scratch, plan holds %zu", need, p->z_bytes);
     DAS_CU(launch_relayout(y, p->z, iq ? p->rot : nullptr, p->storage == DAS_STORE_F32 ? nullptr : p->inv_scale, iq,
-                           p->storage, B, Bs, QM, p->K, s));
+                           p->storage, B, fb, nch, QM, p->K, s));
     p->launches += 1;
     *z_out = p->z;
     return DAS_OK;
@@ -365,6 +373,7 @@ int das_plan_create(das_plan_t **out, const das_geometry_t *geometry, const das_
 
     const long long T = n_tiles(g);
     int rc;
+    cudaError_t e0;
 #define DAS_ALLOC(ptr, bytes, what) \
     if ((rc = dalloc(p, (void **)&(ptr), (bytes), (what))) != DAS_OK) return bail(rc)
     DAS_ALLOC(p->elem_pos, sizeof(double) * 3 * M, "element positions");
@@ -374,6 +383,9 @@ int das_plan_create(das_plan_t **out, const das_geometry_t *geometry, const das_
     DAS_ALLOC(p->tx_off, sizeof(double) * Q, "transmit offsets");
     DAS_ALLOC(p->tx_tb, sizeof(int) * (size_t)T * Q, "transmit bases");
     DAS_ALLOC(p->tx_t, sizeof(float) * (size_t)T * Q * TILE_N, "transmit delays");
+    DAS_ALLOC(p->tx_tmin, sizeof(float) * (size_t)T * Q, "transmit delay minima");
+    DAS_ALLOC(p->err, sizeof(int), "device error word");
+    if ((e0 = cudaMemset(p->err, 0, sizeof(int))) != cudaSuccess) return bail(cuda_fail(e0, "cudaMemset"));
     DAS_ALLOC(p->partial, sizeof(double) * (size_t)T * p->max_batch, "partials");
     DAS_ALLOC(p->scalar, sizeof(double), "scalar");
     p->partial_n = (size_t)T * p->max_batch;
@@ -464,6 +476,20 @@ int das_plan_info(const das_plan_t *plan, das_plan_info_t *info) {
     return DAS_OK;
 }
 
+int das_plan_check(das_plan_t *plan, das_stream_t stream) {
+    if (!plan) return fail(DAS_ERR_INVALID_ARG, "plan is NULL");
+    DeviceGuard guard(plan->device);
+    int flags = 0;
+    DAS_CU(cudaMemcpyAsync(&flags, plan->err, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    DAS_CU(cudaStreamSynchronize((cudaStream_t)stream));
+    if (flags) {
+        DAS_CU(cudaMemsetAsync(plan->err, 0, sizeof(int), (cudaStream_t)stream));
+        DAS_CU(cudaStreamSynchronize((cudaStream_t)stream));
+        return fail(DAS_ERR_TIMEOUT, "a kernel gave up waiting for a staged copy (error word 0x%x)", flags);
+    }
+    return DAS_OK;
+}
+
 int das_plan_enable_timing(das_plan_t *plan, int capacity) {
     if (!plan || capacity < 0) return fail(DAS_ERR_INVALID_ARG, "bad argument");
     DeviceGuard guard(plan->device);
@@ -499,7 +525,8 @@ int das_plan_timing(das_plan_t *plan, double *ms_total, int *launches) {
 
 int das_plan_set_tuning(das_plan_t *plan, const das_tuning_t *tuning) {
     if (!plan || !tuning) return fail(DAS_ERR_INVALID_ARG, "NULL argument");
-    if (tuning->frames_per_thread < 0 || tuning->ctas_per_sm < 0) return fail(DAS_ERR_INVALID_ARG, "negative tuning value");
+    if (tuning->frames_per_thread < 0 || tuning->ctas_per_sm < 0 || tuning->no_staging < 0)
+        return fail(DAS_ERR_INVALID_ARG, "negative tuning value");
     if (tuning->frames_per_thread > 0 &&
         !tile_fb_supported(MODE_FWD, is_iq(plan), plan->storage, tuning->frames_per_thread))
         return fail(DAS_ERR_UNSUPPORTED, "frames_per_thread %d not compiled for this storage", tuning->frames_per_thread);
@@ -528,10 +555,9 @@ int das_forward(das_plan_t *plan, const void *y_dev, void *x_dev, int batch, das
     if ((rc = prepare_if_dirty(plan, s)) != DAS_OK) return rc;
     const int fb = choose_fb(plan, batch, MODE_FWD);
     const int nch = (batch + fb - 1) / fb;
-    const int Bs = nch * fb;
     const void *z = nullptr;
-    if ((rc = stage_channels(plan, y_dev, batch, Bs, s, &z)) != DAS_OK) return rc;
-    TileArgs A = tile_args(plan, Bs, batch, fb, z);
+    if ((rc = stage_channels(plan, y_dev, batch, fb, nch, s, &z)) != DAS_OK) return rc;
+    TileArgs A = tile_args(plan, batch, fb, z);
     A.x = x_dev;
     const bool timed = plan->ev_used < (int)plan->ev_start.size();
     if (timed) DAS_CU(cudaEventRecord(plan->ev_start[plan->ev_used], s));
@@ -619,10 +645,9 @@ int das_grad_c(das_plan_t *plan, const void *y_dev, const void *gx_dev, double *
     if ((rc = prepare_if_dirty(plan, s)) != DAS_OK) return rc;
     const int fb = choose_fb(plan, batch, MODE_DC);
     const int nch = (batch + fb - 1) / fb;
-    const int Bs = nch * fb;
     const void *z = nullptr;
-    if ((rc = stage_channels(plan, y_dev, batch, Bs, s, &z)) != DAS_OK) return rc;
-    TileArgs A = tile_args(plan, Bs, batch, fb, z);
+    if ((rc = stage_channels(plan, y_dev, batch, fb, nch, s, &z)) != DAS_OK) return rc;
+    TileArgs A = tile_args(plan, batch, fb, z);
     A.gx = gx_dev;
     A.partial = plan->partial;
     const long long np = n_tiles(plan->g) * nch;
@@ -640,7 +665,7 @@ int das_count_active(das_plan_t *plan, long long *count_host, das_stream_t strea
     cudaStream_t s = (cudaStream_t)stream;
     int rc;
     if ((rc = prepare_if_dirty(plan, s)) != DAS_OK) return rc;
-    TileArgs A = tile_args(plan, 1, 1, 1, nullptr);
+    TileArgs A = tile_args(plan, 1, 1, nullptr);
     A.partial = plan->partial;
     DAS_CU(launch_tile(A, MODE_COUNT, 0, DAS_STORE_F32, 1, 1, s));
     DAS_CU(launch_reduce(plan->partial, n_tiles(plan->g), plan->scalar, s));
@@ -704,7 +729,6 @@ extern "C" int das_grad_c_static(das_plan_t *plan, const void *y_dev, const void
     if (plan->storage != DAS_STORE_F32) return fail(DAS_ERR_UNSUPPORTED, "das_grad_c_static needs float32 storage");
     const int fb = choose_fb(plan, batch, MODE_DC);
     const int nch = (batch + fb - 1) / fb;
-    const int Bs = nch * fb;
     const long long np = n_tiles(plan->g) * nch;
     if (np > DAS_STATIC_PARTIALS)
         return fail(DAS_ERR_UNSUPPORTED,
@@ -717,8 +741,8 @@ extern "C" int das_grad_c_static(das_plan_t *plan, const void *y_dev, const void
     cudaStream_t s = (cudaStream_t)stream;
     if ((rc = prepare_if_dirty(plan, s)) != DAS_OK) return rc;
     const void *z = nullptr;
-    if ((rc = stage_channels(plan, y_dev, batch, Bs, s, &z)) != DAS_OK) return rc;
-    TileArgs A = tile_args(plan, Bs, batch, fb, z);
+    if ((rc = stage_channels(plan, y_dev, batch, fb, nch, s, &z)) != DAS_OK) return rc;
+    TileArgs A = tile_args(plan, batch, fb, z);
     A.gx = gx_dev;
     A.partial = partial;  // every slot 0..np-1 is written by its CTA before the reduction reads it
     DAS_CU(launch_tile(A, MODE_DC, is_iq(plan), DAS_STORE_F32, fb, nch, s));

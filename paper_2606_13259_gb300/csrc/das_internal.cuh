@@ -61,20 +61,24 @@ __host__ __device__ inline void tile_centre(const GridDesc &g, int tx, int ty, i
     z = g.oz + g.sz * (tz * TILE_Z + 0.5 * (TILE_Z - 1));
 }
 
-// Lane l of a tile holds voxel (l % 8, (l / 8) % 4, l / 32) of the tile.
+// Lane l of a tile: warp l / 32 takes z-layer l / 32 (8 x 4 voxels); each
+// quarter-warp (8 lanes) covers a 4 x 2 patch, so the lanes that load together
+// sit close to each other and mostly need the same sample rows.
 __host__ __device__ inline void lane_offset(int l, int &lx, int &ly, int &lz) {
-    lx = l % TILE_X;
-    ly = (l / TILE_X) % TILE_Y;
-    lz = l / (TILE_X * TILE_Y);
+    const int w = l & 7, qd = (l >> 3) & 3;
+    lx = (w & 3) | ((qd & 1) << 2);
+    ly = (w >> 2) | ((qd >> 1) << 1);
+    lz = l >> 5;
 }
 
 // Arguments of the tile kernels (forward, sound-speed derivative, term count).
 struct TileArgs {
     GridDesc g;
     int M, Q, K;
-    int Bs;        // row stride of the relayouted data, in samples (padded batch)
     int B;         // frames in this call
-    int fb;        // frames per CTA chunk (= template FB)
+    int fb;        // frames per CTA chunk (= template FB) = samples per relayouted row
+    int umax;      // rows per staged sample window (TMA kernels)
+    float win_lo;  // a * tile radius + margin: lower reach of a window below the tile reference (samples)
     double ad;     // fs / c, float64
     float a;       // fs / c, float32
     float theta;   // 2 pi f_d / fs
@@ -86,9 +90,11 @@ struct TileArgs {
     const float4 *elem_nrm;    // [M] (nx, ny, nz, 0)
     const int *tx_tb;          // [tiles][Q] integer transmit base
     const float *tx_t;         // [tiles][Q][128] transmit rest per voxel
+    const float *tx_tmin;      // [tiles][Q] smallest transmit rest over the tile's voxels
     const float *w_tx;         // [tiles][Q][128] transmit weight, or null
     const float *scale;        // [Q][M] storage scale, or null
-    const void *z;             // channel data [Q][M][K][Bs]
+    const void *z;             // channel data [chunk][Q][M][K][fb] (chunk-major)
+    int *err;                  // device error flags (bit 0: a staged-copy wait timed out)
     void *x;                   // image [B][N] (MODE_FWD)
     const void *gx;            // cotangent [B][N] (MODE_DC)
     double *partial;           // per-CTA partial sums (MODE_DC, MODE_COUNT)
@@ -119,14 +125,18 @@ struct AdjArgs {
 
 // Kernel launchers (defined in the .cu files).
 cudaError_t launch_prepare(const GridDesc &g, int Q, const int *kind, const double *vec, const double *off,
-                           const double *t0, double ad, int *tx_tb, float *tx_t, cudaStream_t s);
+                           const double *t0, double ad, int *tx_tb, float *tx_t, float *tx_tmin, cudaStream_t s);
+// y[b][qm][k] -> z[c][qm][k][fb] with b = c * fb + j; frames B .. nch*fb-1 are zero.
 cudaError_t launch_relayout(const void *y, void *z, const float2 *rot, const float *inv_scale, int iq, int store,
-                            int B, int Bs, int QM, int K, cudaStream_t s);
+                            int B, int fb, int nch, int QM, int K, cudaStream_t s);
 cudaError_t launch_scale(const void *y, float *scale, float *inv_scale, int iq, int store, int B, int QM, int K,
                          cudaStream_t s);
 cudaError_t launch_tile(const TileArgs &args, int mode, int iq, int store, int fb, int n_chunks, cudaStream_t s);
 cudaError_t launch_adjoint(const AdjArgs &args, int iq, cudaStream_t s);
 cudaError_t launch_reduce(const double *partial, long long n, double *out, cudaStream_t s);
 bool tile_fb_supported(int mode, int iq, int store, int fb);
+// Rows of a staged window: every (voxel, element, transmit) of a tile falls in
+// [Tb + Rb + floor(rf + tmin - a R), + 4 a R + 3], R the tile radius.
+int window_rows(double a_R);
 
 }  // namespace das

@@ -27,18 +27,22 @@ __device__ inline double tx_path(int kind, double vx, double vy, double vz, doub
     return 0.0;
 }
 
-// One CTA per tile, one thread per voxel lane.
+// One CTA per tile, one thread per voxel lane.  Also records, per (tile,
+// transmit), the smallest float32 rest over the tile's voxels: together with
+// the tile radius it bounds the sample rows any voxel of the tile can need.
 __global__ void __launch_bounds__(TILE_N) prepare_kernel(GridDesc g, int Q, const int *__restrict__ kind,
                                                          const double *__restrict__ vec,
                                                          const double *__restrict__ off, double t0x, double t0y,
                                                          double t0z, double ad, int *__restrict__ tx_tb,
-                                                         float *__restrict__ tx_t) {
+                                                         float *__restrict__ tx_t, float *__restrict__ tx_tmin) {
+    __shared__ float red[TILE_N / 32];
     const long long tile = blockIdx.x;
     const int tx = (int)(tile % g.tiles_x);
     const int ty = (int)((tile / g.tiles_x) % g.tiles_y);
     const int tz = (int)(tile / ((long long)g.tiles_x * g.tiles_y));
     int lx, ly, lz;
     lane_offset(threadIdx.x, lx, ly, lz);
+    const bool valid = tx * TILE_X + lx < g.nx && ty * TILE_Y + ly < g.ny && tz * TILE_Z + lz < g.nz;
     double cx, cy, cz;
     tile_centre(g, tx, ty, tz, cx, cy, cz);
     const double px = g.ox + g.sx * (tx * TILE_X + lx);
@@ -48,18 +52,31 @@ __global__ void __launch_bounds__(TILE_N) prepare_kernel(GridDesc g, int Q, cons
         const int kd = kind[q];
         const double vx = vec[3 * q], vy = vec[3 * q + 1], vz = vec[3 * q + 2], o = off[q];
         const double base = floor(ad * tx_path(kd, vx, vy, vz, o, t0x, t0y, t0z, cx, cy, cz));
-        const double t = ad * tx_path(kd, vx, vy, vz, o, t0x, t0y, t0z, px, py, pz) - base;
-        tx_t[(tile * Q + q) * TILE_N + threadIdx.x] = (float)t;
+        const float t = (float)(ad * tx_path(kd, vx, vy, vz, o, t0x, t0y, t0z, px, py, pz) - base);
+        tx_t[(tile * Q + q) * TILE_N + threadIdx.x] = t;
         if (threadIdx.x == 0) tx_tb[tile * Q + q] = (int)base;
+        float mn = valid ? t : 3.0e38f;
+        for (int d = 16; d > 0; d >>= 1) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, d));
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mn;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float m = red[0];
+            for (int w = 1; w < TILE_N / 32; ++w) m = fminf(m, red[w]);
+            tx_tmin[tile * Q + q] = m;
+        }
+        __syncthreads();
     }
 }
 
 cudaError_t launch_prepare(const GridDesc &g, int Q, const int *kind, const double *vec, const double *off,
-                           const double *t0, double ad, int *tx_tb, float *tx_t, cudaStream_t s) {
+                           const double *t0, double ad, int *tx_tb, float *tx_t, float *tx_tmin, cudaStream_t s) {
     const long long nt = n_tiles(g);
-    prepare_kernel<<<(unsigned)nt, TILE_N, 0, s>>>(g, Q, kind, vec, off, t0[0], t0[1], t0[2], ad, tx_tb, tx_t);
+    prepare_kernel<<<(unsigned)nt, TILE_N, 0, s>>>(g, Q, kind, vec, off, t0[0], t0[1], t0[2], ad, tx_tb, tx_t,
+                                                   tx_tmin);
     return cudaGetLastError();
 }
+
+int window_rows(double a_R) { return (int)ceil(4.0 * a_R) + 4; }
 
 // ---------------------------------------------------------------------------
 // storage conversion helpers
@@ -121,12 +138,15 @@ cudaError_t launch_scale(const void *y, float *scale, float *inv_scale, int iq, 
 // ---------------------------------------------------------------------------
 
 // Batched: 32 frames x 32 samples per step through shared memory; reads are
-// contiguous along k, writes contiguous along b.  Frames B..Bs-1 are zero.
+// contiguous along k, writes contiguous along the frames of a chunk.  The
+// output is chunk-major, z[c][qm][k][fb] holding frame b = c * fb + j, so the
+// rows one CTA of the tile kernels reads are contiguous.  Frames B .. Bs-1
+// (Bs = chunks * fb) are zero.
 template <bool IQ, int ST>
 __global__ void __launch_bounds__(256) relayout_kernel(const void *__restrict__ y_, void *__restrict__ z_,
                                                        const float2 *__restrict__ rot,
-                                                       const float *__restrict__ inv_scale, int B, int Bs, int QM,
-                                                       int K) {
+                                                       const float *__restrict__ inv_scale, int B, int fb, int Bs,
+                                                       int QM, int K) {
     using OutC = typename StoreT<ST>::c;
     using OutR = typename StoreT<ST>::r;
     __shared__ float2 tile[32][33];
@@ -152,7 +172,8 @@ __global__ void __launch_bounds__(256) relayout_kernel(const void *__restrict__ 
             const int kl = ty + 8 * i, k = k0 + kl, b = bc + tx;
             if (k < K && b < Bs) {
                 float2 v = tile[tx][kl];
-                const size_t o = ((size_t)qm * K + k) * (size_t)Bs + b;
+                const int c = b / fb, j = b - c * fb;
+                const size_t o = (((size_t)c * QM + qm) * K + k) * (size_t)fb + j;
                 if (IQ) {
                     if (rot) v = cmul(v, rot[k]);
                     v.x *= s;
@@ -192,28 +213,29 @@ __global__ void __launch_bounds__(256) convert1_kernel(const void *__restrict__ 
 }
 
 template <bool IQ, int ST>
-static void relayout_dispatch(const void *y, void *z, const float2 *rot, const float *inv_scale, int B, int Bs, int QM,
-                              int K, cudaStream_t s) {
+static void relayout_dispatch(const void *y, void *z, const float2 *rot, const float *inv_scale, int B, int fb,
+                              int nch, int QM, int K, cudaStream_t s) {
+    const int Bs = fb * nch;
     if (Bs == 1) {
         const size_t total = (size_t)QM * K;
         const int blocks = (int)((total + 255) / 256 < 152 * 32 ? (total + 255) / 256 : 152 * 32);
         convert1_kernel<IQ, ST><<<blocks, 256, 0, s>>>(y, z, rot, inv_scale, QM, K);
     } else {
         dim3 grid((K + 31) / 32, QM < 65535 ? QM : 65535);
-        relayout_kernel<IQ, ST><<<grid, 256, 0, s>>>(y, z, rot, inv_scale, B, Bs, QM, K);
+        relayout_kernel<IQ, ST><<<grid, 256, 0, s>>>(y, z, rot, inv_scale, B, fb, Bs, QM, K);
     }
 }
 
 cudaError_t launch_relayout(const void *y, void *z, const float2 *rot, const float *inv_scale, int iq, int store,
-                            int B, int Bs, int QM, int K, cudaStream_t s) {
+                            int B, int fb, int nch, int QM, int K, cudaStream_t s) {
     if (iq) {
-        if (store == ST_F32) relayout_dispatch<true, ST_F32>(y, z, rot, inv_scale, B, Bs, QM, K, s);
-        else if (store == ST_F16) relayout_dispatch<true, ST_F16>(y, z, rot, inv_scale, B, Bs, QM, K, s);
-        else relayout_dispatch<true, ST_BF16>(y, z, rot, inv_scale, B, Bs, QM, K, s);
+        if (store == ST_F32) relayout_dispatch<true, ST_F32>(y, z, rot, inv_scale, B, fb, nch, QM, K, s);
+        else if (store == ST_F16) relayout_dispatch<true, ST_F16>(y, z, rot, inv_scale, B, fb, nch, QM, K, s);
+        else relayout_dispatch<true, ST_BF16>(y, z, rot, inv_scale, B, fb, nch, QM, K, s);
     } else {
-        if (store == ST_F32) relayout_dispatch<false, ST_F32>(y, z, rot, inv_scale, B, Bs, QM, K, s);
-        else if (store == ST_F16) relayout_dispatch<false, ST_F16>(y, z, rot, inv_scale, B, Bs, QM, K, s);
-        else relayout_dispatch<false, ST_BF16>(y, z, rot, inv_scale, B, Bs, QM, K, s);
+        if (store == ST_F32) relayout_dispatch<false, ST_F32>(y, z, rot, inv_scale, B, fb, nch, QM, K, s);
+        else if (store == ST_F16) relayout_dispatch<false, ST_F16>(y, z, rot, inv_scale, B, fb, nch, QM, K, s);
+        else relayout_dispatch<false, ST_BF16>(y, z, rot, inv_scale, B, fb, nch, QM, K, s);
     }
     return cudaGetLastError();
 }

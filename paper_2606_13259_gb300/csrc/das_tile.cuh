@@ -193,9 +193,10 @@ __global__ void __launch_bounds__(TILE_N, TileOcc<FB>::v) tile_kernel(const Tile
             const float d = sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
             const float num = fmaf(2.f, fmaf(G.x, dx, fmaf(G.y, dy, G.z * dz)), dd);
             const float r = Nn.w + A.a * __fdividef(num, d + G.w);
+            // chunk-major rows: z[chunk][q][m][k][FB]
             const unsigned char *zrow = reinterpret_cast<const unsigned char *>(A.z) +
-                                        ((size_t)mm * A.K * A.Bs + (size_t)b0) * SZ;
-            const size_t qstride = (size_t)A.M * A.K * A.Bs * SZ;
+                                        (((size_t)blockIdx.y * Q * A.M + mm) * A.K) * (size_t)(FB * SZ);
+            const size_t qstride = (size_t)A.M * A.K * (FB * SZ);
 #pragma unroll 2
             for (int q = 0; q < Q; ++q) {
                 const float f = r + s_t[q * TILE_N + tid];
@@ -235,8 +236,8 @@ __global__ void __launch_bounds__(TILE_N, TileOcc<FB>::v) tile_kernel(const Tile
                         c1r = s;
                     }
                 }
-                const unsigned char *p0 = zrow + q * qstride + (size_t)k * A.Bs * SZ;
-                const unsigned char *p1 = p0 + (size_t)A.Bs * SZ;
+                const unsigned char *p0 = zrow + q * qstride + (size_t)k * (FB * SZ);
+                const unsigned char *p1 = p0 + FB * SZ;
                 uint32_t w0[Row::NW], w1[Row::NW];
                 Row::load(p0, w0);
                 Row::load(p1, w1);

@@ -1,13 +1,13 @@
 // das_tile_bf16.cu -- tile-kernel instances for bf16 storage with a float32
 // scale per (transmit, element) (Sec. 3.3, mixed-precision storage); forward only.
-#include "das_tile.cuh"
+#include "das_tile_tma.cuh"
 
 namespace das {
 
 #define DAS_BF16_CASE(FB)                                                                            \
     case FB:                                                                                          \
-        return iq ? launch_tile_t<FB, true, ST_BF16, MODE_FWD>(A, n_chunks, s)                       \
-                  : launch_tile_t<FB, false, ST_BF16, MODE_FWD>(A, n_chunks, s);
+        return iq ? launch_tile_best<FB, true, ST_BF16, MODE_FWD>(A, n_chunks, s)                       \
+                  : launch_tile_best<FB, false, ST_BF16, MODE_FWD>(A, n_chunks, s);
 
 cudaError_t launch_tile_bf16(const TileArgs &A, int mode, int iq, int fb, int n_chunks, cudaStream_t s) {
     if (mode != MODE_FWD) return cudaErrorInvalidValue;

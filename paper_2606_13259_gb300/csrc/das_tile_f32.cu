@@ -1,16 +1,16 @@
 // das_tile_f32.cu -- tile-kernel instances for float32 storage (forward,
 // sound-speed derivative, term count).
-#include "das_tile.cuh"
+#include "das_tile_tma.cuh"
 
 namespace das {
 
 #define DAS_F32_CASE(FB)                                                                              \
     case FB:                                                                                          \
         if (mode == MODE_FWD)                                                                         \
-            return iq ? launch_tile_t<FB, true, ST_F32, MODE_FWD>(A, n_chunks, s)                     \
-                      : launch_tile_t<FB, false, ST_F32, MODE_FWD>(A, n_chunks, s);                   \
-        return iq ? launch_tile_t<FB, true, ST_F32, MODE_DC>(A, n_chunks, s)                          \
-                  : launch_tile_t<FB, false, ST_F32, MODE_DC>(A, n_chunks, s);
+            return iq ? launch_tile_best<FB, true, ST_F32, MODE_FWD>(A, n_chunks, s)                     \
+                      : launch_tile_best<FB, false, ST_F32, MODE_FWD>(A, n_chunks, s);                   \
+        return iq ? launch_tile_best<FB, true, ST_F32, MODE_DC>(A, n_chunks, s)                          \
+                  : launch_tile_best<FB, false, ST_F32, MODE_DC>(A, n_chunks, s);
 
 cudaError_t launch_tile_f32(const TileArgs &A, int mode, int iq, int fb, int n_chunks, cudaStream_t s) {
     if (mode == MODE_COUNT) return launch_tile_t<1, false, ST_F32, MODE_COUNT>(A, 1, s);

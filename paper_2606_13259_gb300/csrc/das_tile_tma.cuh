@@ -1,0 +1,413 @@
+// das_tile_tma.cuh -- the voxel-tile kernel with TMA-staged sample windows.
+//
+// Same work and same arithmetic as tile_kernel (das_tile.cuh): one CTA per
+// tile of 8 x 4 x 4 voxels and chunk of FB frames, one voxel per thread, FB
+// accumulators in registers, no atomics.  The difference is how the two
+// interpolation taps reach the registers.  For every (element, transmit) item
+// the rows any voxel of the tile can need form one contiguous window of
+// `umax` rows of z[chunk][q][m][.][FB]; thread 0 brings it into shared memory
+// with a single bulk asynchronous copy (cp.async.bulk, completion counted on
+// an mbarrier), TMA_STAGES items ahead of the consumers.  Threads then read
+// their two rows from shared memory, where lanes of a quarter-warp that need
+// up to four different rows do not conflict, instead of from L1, where every
+// distinct line costs a separate data-return wavefront.
+//
+// Window bound: with f = rf + t + delta the fractional delay of a voxel,
+// |delta| <= a R (R the tile radius) and t >= tmin (per tile and transmit,
+// from the prepare kernel), so floor(f) >= floor(rf + tmin - a R) and the
+// span of floor(f) + 1 over the tile is at most 4 a R + 3 rows.  A voxel whose
+// rows fall outside the window anyway reads them from global memory.
+//
+// Waits on the mbarriers are bounded; on expiry the kernel sets bit 0 of the
+// plan's error word, waits (bounded) for the copies it has in flight and
+// returns.
+#pragma once
+
+#include "das_tile.cuh"
+
+namespace das {
+
+constexpr int TMA_STAGES = 4;
+constexpr uint32_t TMA_WAIT_LIMIT = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    for (uint32_t i = 0; i < TMA_WAIT_LIMIT; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// Global -> shared bulk copy of `bytes` (multiple of 16, both ends 16-byte
+// aligned), completion reported to `bar` as transaction bytes.
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ uint4 lds128(uint32_t addr) {
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "r"(addr));
+    return v;
+}
+
+// First row and row count of the staged window of one (element, transmit).
+__device__ __forceinline__ void item_window(int tb, int rb, float rf, float tmin, float win_lo, int umax, int K,
+                                            int &ks, int &cnt) {
+    const int kw0 = tb + rb + (int)floorf(rf + tmin - win_lo);
+    const int kend = min(kw0 + umax, K);
+    ks = max(kw0, 0);
+    cnt = max(kend - ks, 0);
+}
+
+template <int FB, bool IQ, int ST, int MODE>
+__global__ void __launch_bounds__(TILE_N, TileOcc<FB>::v) tile_tma_kernel(const TileArgs A) {
+    using Row = FrameRow<FB, IQ, ST>;
+    constexpr int SZ = Row::SZ;
+    constexpr int RB = FB * SZ;  // bytes per staged row
+    static_assert(RB % 16 == 0, "staged rows must be whole 16-byte vectors");
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int Q = A.Q;
+    const int umax = A.umax;
+    const bool has_w = A.w_tx != nullptr;
+    unsigned char *stages = smem;                                                        // [S][umax][RB]
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(stages + (size_t)TMA_STAGES * umax * RB);  // [S]
+    float4 *s_eg = reinterpret_cast<float4 *>(mbar + TMA_STAGES);                       // [128]
+    float4 *s_en = s_eg + TILE_N;                                                        // [128]
+    float *s_t = reinterpret_cast<float *>(s_en + TILE_N);                              // [Q][128]
+    float *s_w = s_t + Q * TILE_N;                                                       // [Q][128]
+    float *s_tmin = s_w + (has_w ? Q * TILE_N : 0);                                      // [Q]
+    int *s_erb = reinterpret_cast<int *>(s_tmin + Q);                                    // [128]
+    int *s_em = s_erb + TILE_N;                                                          // [128]
+    int *s_tb = s_em + TILE_N;                                                           // [Q]
+    int *s_cnt = s_tb + Q;                                                               // [4]
+    int *s_abort = s_cnt + 4;                                                            // [1]
+
+    const int tid = threadIdx.x;
+    const long long tile = blockIdx.x;
+    const int b0 = blockIdx.y * FB;
+    const GridDesc &g = A.g;
+    const int tx = (int)(tile % g.tiles_x);
+    const int ty = (int)((tile / g.tiles_x) % g.tiles_y);
+    const int tz = (int)(tile / ((long long)g.tiles_x * g.tiles_y));
+    int lx, ly, lz;
+    lane_offset(tid, lx, ly, lz);
+    const int ix = tx * TILE_X + lx, iy = ty * TILE_Y + ly, iz = tz * TILE_Z + lz;
+    const bool valid = ix < g.nx && iy < g.ny && iz < g.nz;
+    const long long n = ((long long)iz * g.ny + iy) * g.nx + ix;
+    double p0x, p0y, p0z;
+    tile_centre(g, tx, ty, tz, p0x, p0y, p0z);
+    const float dx = (float)(g.sx * (lx - 0.5 * (TILE_X - 1)));
+    const float dy = (float)(g.sy * (ly - 0.5 * (TILE_Y - 1)));
+    const float dz = (float)(g.sz * (lz - 0.5 * (TILE_Z - 1)));
+    const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const unsigned char *zc = reinterpret_cast<const unsigned char *>(A.z) +
+                              (size_t)blockIdx.y * Q * A.M * A.K * (size_t)RB;  // this chunk
+    const size_t qstride = (size_t)A.M * A.K * RB;
+
+    for (int q = 0; q < Q; ++q) {
+        s_t[q * TILE_N + tid] = A.tx_t[(tile * Q + q) * TILE_N + tid];
+        if (has_w) s_w[q * TILE_N + tid] = A.w_tx[(tile * Q + q) * TILE_N + tid];
+    }
+    for (int q = tid; q < Q; q += TILE_N) {
+        s_tb[q] = A.tx_tb[tile * Q + q];
+        s_tmin[q] = A.tx_tmin[tile * Q + q];
+    }
+    if (tid == 0) {
+        for (int s = 0; s < TMA_STAGES; ++s) mbar_init(&mbar[s], 1);
+        mbar_init_fence();
+        *s_abort = 0;
+    }
+
+    float acc_r[FB], acc_i[FB];
+#pragma unroll
+    for (int b = 0; b < FB; ++b) acc_r[b] = acc_i[b] = 0.f;
+
+    // Thread 0 stages item i (element j = i / Q, transmit q = i % Q) of the
+    // current element block into stage (g0 + i) % S.
+    auto issue = [&](long long g0, int i) {
+        const int j = i / Q, q = i - j * Q;
+        const long long gi = g0 + i;
+        uint64_t *bar = &mbar[gi % TMA_STAGES];
+        int ks, cnt;
+        item_window(s_tb[q], s_erb[j], s_en[j].w, s_tmin[q], A.win_lo, umax, A.K, ks, cnt);
+        if (cnt > 0) {
+            const uint32_t bytes = (uint32_t)cnt * RB;
+            mbar_arrive_expect_tx(bar, bytes);
+            bulk_copy_g2s(stages + (size_t)(gi % TMA_STAGES) * umax * RB,
+                          zc + q * qstride + ((size_t)s_em[j] * A.K + ks) * RB, bytes, bar);
+        } else {
+            mbar_arrive(bar);
+        }
+    };
+
+    const int lane = tid & 31, warp = tid >> 5;
+    long long g0 = 0;  // items staged in earlier element blocks (mbarrier phase bookkeeping)
+    bool aborted = false;
+    for (int m0 = 0; m0 < A.M && !aborted; m0 += TILE_N) {
+        __syncthreads();  // previous block's records and stages are no longer read
+        const int m = m0 + tid;
+        bool cand = false;
+        float4 eg = make_float4(0.f, 0.f, 0.f, 0.f), en = eg;
+        int rb = 0;
+        if (m < A.M) {
+            const double rx = A.elem_pos[3 * m], ry = A.elem_pos[3 * m + 1], rz = A.elem_pos[3 * m + 2];
+            const double Gx = p0x - rx, Gy = p0y - ry, Gz = p0z - rz;
+            const double D0 = sqrt(Gx * Gx + Gy * Gy + Gz * Gz);
+            const double R0 = A.ad * D0;
+            const double Rf = floor(R0);
+            rb = (int)Rf;
+            const float4 nn = A.elem_nrm[m];
+            eg = make_float4((float)Gx, (float)Gy, (float)Gz, (float)D0);
+            en = make_float4(nn.x, nn.y, nn.z, (float)(R0 - Rf));
+            cand = true;
+            if (A.thr >= 0.f) {
+                const float z0 = eg.x * nn.x + eg.y * nn.y + eg.z * nn.z;
+                const float cx = eg.y * nn.z - eg.z * nn.y, cy = eg.z * nn.x - eg.x * nn.z,
+                            cz = eg.x * nn.y - eg.y * nn.x;
+                const float rho0 = sqrtf(cx * cx + cy * cy + cz * cz);
+                const float zmax = z0 + A.tile_radius;
+                const float rmin = fmaxf(rho0 - A.tile_radius, 0.f);
+                cand = (zmax > 0.f) && (rmin * rmin <= A.thr * zmax * zmax * 1.001f);
+            }
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, cand);
+        if (lane == 0) s_cnt[warp] = __popc(bal);
+        __syncthreads();
+        int off = 0;
+        for (int w = 0; w < warp; ++w) off += s_cnt[w];
+        if (cand) {
+            const int idx = off + __popc(bal & ((1u << lane) - 1u));
+            s_eg[idx] = eg;
+            s_en[idx] = en;
+            s_erb[idx] = rb;
+            s_em[idx] = m;
+        }
+        const int total = s_cnt[0] + s_cnt[1] + s_cnt[2] + s_cnt[3];
+        __syncthreads();
+
+        const int n_items = total * Q;
+        if (tid == 0)
+            for (int i = 0; i < TMA_STAGES && i < n_items; ++i) issue(g0, i);
+
+        int j = 0, q = 0;
+        bool inside = false;
+        float r = 0.f;
+        float4 G = make_float4(0.f, 0.f, 0.f, 0.f), Nn = G;
+        int Rb = 0, mm = 0;
+        for (int i = 0; i < n_items; ++i) {
+            if (q == 0) {
+                // (voxel, element) part of the geometry, once per element
+                G = s_eg[j];
+                Nn = s_en[j];
+                Rb = s_erb[j];
+                mm = s_em[j];
+                const float ex = G.x + dx, ey = G.y + dy, ez = G.z + dz;
+                inside = valid;
+                if (A.thr >= 0.f) {
+                    const float zax = fmaf(ex, Nn.x, fmaf(ey, Nn.y, ez * Nn.z));
+                    const float cx = fmaf(ey, Nn.z, -ez * Nn.y), cy = fmaf(ez, Nn.x, -ex * Nn.z),
+                                cz = fmaf(ex, Nn.y, -ey * Nn.x);
+                    const float rho2 = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
+                    inside = inside && (zax > 0.f) && (rho2 <= A.thr * zax * zax);
+                }
+                const float d = sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
+                const float num = fmaf(2.f, fmaf(G.x, dx, fmaf(G.y, dy, G.z * dz)), dd);
+                r = Nn.w + A.a * __fdividef(num, d + G.w);
+            }
+            const long long gi = g0 + i;
+            const int st = (int)(gi % TMA_STAGES);
+            if (!mbar_wait_bounded(&mbar[st], (uint32_t)((gi / TMA_STAGES) & 1))) {
+                atomicOr(A.err, 1);
+                *s_abort = 1;
+            }
+            const float f = r + s_t[q * TILE_N + tid];
+            const float fl = floorf(f);
+            const float al = f - fl;
+            const int k = s_tb[q] + Rb + (int)fl;
+            if (inside && (unsigned)k <= (unsigned)(A.K - 2)) {
+                float w = has_w ? s_w[q * TILE_N + tid] : 1.f;
+                if (ST != ST_F32) w *= __ldg(A.scale + (size_t)q * A.M + mm);
+                float c0r, c0i = 0.f, c1r, c1i = 0.f;
+                if constexpr (IQ) {
+                    float sn, cs;
+                    __sincosf(A.theta * (al - 0.5f), &sn, &cs);
+                    const float uhr = cs * A.hr - sn * A.hi, uhi = cs * A.hi + sn * A.hr;
+                    const float ubr = cs * A.hr + sn * A.hi, ubi = sn * A.hr - cs * A.hi;
+                    if constexpr (MODE == MODE_FWD) {
+                        const float w0 = w * (1.f - al), w1 = w * al;
+                        c0r = w0 * uhr; c0i = w0 * uhi;
+                        c1r = w1 * ubr; c1i = w1 * ubi;
+                    } else {
+                        const float s = -w * ((float)k + al) * (float)A.inv_c;
+                        const float a0 = A.theta * (1.f - al), a1 = A.theta * al;
+                        c0r = s * (-uhr - a0 * uhi); c0i = s * (a0 * uhr - uhi);
+                        c1r = s * (ubr - a1 * ubi); c1i = s * (ubi + a1 * ubr);
+                    }
+                } else {
+                    if constexpr (MODE == MODE_FWD) {
+                        c0r = w * (1.f - al);
+                        c1r = w * al;
+                    } else {
+                        const float s = -w * ((float)k + al) * (float)A.inv_c;
+                        c0r = -s;
+                        c1r = s;
+                    }
+                }
+                int ks, cnt;
+                item_window(s_tb[q], Rb, Nn.w, s_tmin[q], A.win_lo, umax, A.K, ks, cnt);
+                const int u = k - ks;
+                uint32_t w0[Row::NW], w1[Row::NW];
+                if (u >= 0 && u + 1 < cnt) {
+                    const uint32_t a0 = smem_addr(stages) + (uint32_t)((st * umax + u) * RB);
+#pragma unroll
+                    for (int v = 0; v < Row::NW / 4; ++v) {
+                        const uint4 x0 = lds128(a0 + 16 * v), x1 = lds128(a0 + RB + 16 * v);
+                        w0[4 * v] = x0.x; w0[4 * v + 1] = x0.y; w0[4 * v + 2] = x0.z; w0[4 * v + 3] = x0.w;
+                        w1[4 * v] = x1.x; w1[4 * v + 1] = x1.y; w1[4 * v + 2] = x1.z; w1[4 * v + 3] = x1.w;
+                    }
+                } else {
+                    const unsigned char *p0 = zc + q * qstride + ((size_t)mm * A.K + k) * RB;
+                    Row::load(p0, w0);
+                    Row::load(p0 + RB, w1);
+                }
+#pragma unroll
+                for (int b = 0; b < FB; ++b) {
+                    const float2 z0 = Row::get(w0, b), z1 = Row::get(w1, b);
+                    if constexpr (IQ) {
+                        acc_r[b] = fmaf(c0r, z0.x, fmaf(-c0i, z0.y, fmaf(c1r, z1.x, fmaf(-c1i, z1.y, acc_r[b]))));
+                        acc_i[b] = fmaf(c0r, z0.y, fmaf(c0i, z0.x, fmaf(c1r, z1.y, fmaf(c1i, z1.x, acc_i[b]))));
+                    } else {
+                        acc_r[b] = fmaf(c0r, z0.x, fmaf(c1r, z1.x, acc_r[b]));
+                    }
+                }
+            }
+            __syncthreads();  // stage st is free again
+            if (*s_abort) {
+                aborted = true;
+                if (tid == 0) {
+                    // copies that may still be in flight: items i .. i+S-1 were issued
+                    for (int d = 0; d < TMA_STAGES && i + d < n_items; ++d) {
+                        const long long gd = gi + d;
+                        mbar_wait_bounded(&mbar[gd % TMA_STAGES], (uint32_t)((gd / TMA_STAGES) & 1));
+                    }
+                }
+                break;
+            }
+            if (tid == 0 && i + TMA_STAGES < n_items) issue(g0, i + TMA_STAGES);
+            if (++q == Q) {
+                q = 0;
+                ++j;
+            }
+        }
+        g0 += n_items;
+    }
+    if (aborted) return;
+
+    if constexpr (MODE == MODE_FWD) {
+        if (valid) {
+#pragma unroll
+            for (int b = 0; b < FB; ++b) {
+                if (b0 + b < A.B) {
+                    const size_t o = (size_t)(b0 + b) * g.n_voxels + n;
+                    if constexpr (IQ) reinterpret_cast<float2 *>(A.x)[o] = make_float2(acc_r[b], acc_i[b]);
+                    else reinterpret_cast<float *>(A.x)[o] = acc_r[b];
+                }
+            }
+        }
+    } else {
+        double v = 0.0;
+        if (valid) {
+#pragma unroll
+            for (int b = 0; b < FB; ++b) {
+                if (b0 + b < A.B) {
+                    const size_t o = (size_t)(b0 + b) * g.n_voxels + n;
+                    if constexpr (IQ) {
+                        const float2 gv = reinterpret_cast<const float2 *>(A.gx)[o];
+                        v += (double)gv.x * acc_r[b] + (double)gv.y * acc_i[b];
+                    } else {
+                        v += (double)reinterpret_cast<const float *>(A.gx)[o] * acc_r[b];
+                    }
+                }
+            }
+        }
+        __shared__ double red[TILE_N / 32];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp] = v;
+        __syncthreads();
+        if (tid == 0) {
+            double s = 0.0;
+            for (int w = 0; w < TILE_N / 32; ++w) s += red[w];
+            A.partial[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = s;
+        }
+    }
+}
+
+inline size_t tile_tma_smem_bytes(int Q, bool has_w, int umax, int rb) {
+    return (size_t)TMA_STAGES * umax * rb + sizeof(uint64_t) * TMA_STAGES + sizeof(float4) * 2 * TILE_N +
+           sizeof(float) * ((size_t)Q * TILE_N * (has_w ? 2 : 1) + Q) + sizeof(int) * (2 * TILE_N + Q + 5);
+}
+
+template <int FB, bool IQ, int ST, int MODE>
+cudaError_t launch_tile_tma_t(const TileArgs &A, int n_chunks, cudaStream_t s) {
+    constexpr int RB = FB * SampleSize<IQ, ST>::v;
+    const size_t smem = tile_tma_smem_bytes(A.Q, A.w_tx != nullptr, A.umax, RB);
+    auto kern = tile_tma_kernel<FB, IQ, ST, MODE>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)n_tiles(A.g), (unsigned)n_chunks);
+    kern<<<grid, TILE_N, smem, s>>>(A);
+    return cudaGetLastError();
+}
+
+// The staged kernel where its rows are whole 16-byte vectors, staging is on
+// (umax > 0) and the window buffers fit comfortably in shared memory; the
+// plain tile kernel otherwise.
+template <int FB, bool IQ, int ST, int MODE>
+cudaError_t launch_tile_best(const TileArgs &A, int n_chunks, cudaStream_t s) {
+    constexpr int RB = FB * SampleSize<IQ, ST>::v;
+    if constexpr (RB % 16 == 0) {
+        if (A.umax > 0 && tile_tma_smem_bytes(A.Q, A.w_tx != nullptr, A.umax, RB) <= 96 * 1024)
+            return launch_tile_tma_t<FB, IQ, ST, MODE>(A, n_chunks, s);
+    }
+    return launch_tile_t<FB, IQ, ST, MODE>(A, n_chunks, s);
+}
+
+}  // namespace das

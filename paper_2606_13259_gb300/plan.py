@@ -122,9 +122,13 @@ class Plan:
         L.check(self._lib.das_plan_info(self._h, C.byref(i)))
         return {f: getattr(i, f) for f, _ in L.PlanInfo._fields_}
 
-    def set_tuning(self, frames_per_thread: int = 0, ctas_per_sm: int = 0) -> None:
-        t = L.Tuning(int(frames_per_thread), int(ctas_per_sm))
+    def set_tuning(self, frames_per_thread: int = 0, ctas_per_sm: int = 0, staging: bool = True) -> None:
+        t = L.Tuning(int(frames_per_thread), int(ctas_per_sm), 0 if staging else 1)
         L.check(self._lib.das_plan_set_tuning(self._h, C.byref(t)))
+
+    def check(self, stream=None) -> None:
+        """Wait for the stream; raise if a kernel recorded a failure (a bounded wait that expired)."""
+        L.check(self._lib.das_plan_check(self._h, _stream(stream)))
 
     def enable_timing(self, capacity: int) -> None:
         """Record CUDA events around the DAS kernel of the next `capacity` forward calls."""
