@@ -38,6 +38,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["paper", "batched"], default="paper",
+                    help="paper: the 128^3 x 1024 x 16 forward; batched: three uneven plans, 64 frames, one launch")
     ap.add_argument("--frames", type=int, default=20)
     ap.add_argument("--K", type=int, default=2048, help="samples per channel (all delays lie below 400)")
     ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32")
@@ -224,10 +226,84 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batched(args):
+    """Batched form: 64 FP16 IQ frames drawn from three uneven plans (frame f
+    belongs to plan f mod 3), all in one persistent launch replayed from a CUDA
+    graph, launch shape from the autotuner."""
+    import torch
+
+    from paper_2606_13259_gb300 import Batch, Plan, autotune
+    from paper_2606_13259_gb300 import build as B
+    from paper_2606_13259_gb300 import synth as S
+
+    torch.cuda.set_device(0)
+    B.build()
+    scenes = S.scenes_batched()
+    total = 64
+    frames = [len(range(i, total, 3)) for i in range(3)]
+    ys = [S.frames(sc, f, seed=4 + 100000 * i, n_speckle=20000, points=S.paper_points(sc), device="cuda")
+          for i, (sc, f) in enumerate(zip(scenes, frames))]
+    plans = [Plan.from_scene(sc, storage=args.storage if args.storage != "f32" else "f16", max_batch=f)
+             for sc, f in zip(scenes, frames)]
+    batch = Batch(plans, frames)
+    outs = [torch.empty((f,) + p.shape, dtype=torch.complex64, device="cuda") for p, f in zip(plans, frames)]
+    tuned = autotune.tune_batch(batch, ys, outs, reps=2)
+    for _ in range(args.warmup):
+        batch.forward(ys, outs)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.3)
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(args.steps):
+        batch.forward(ys, outs)
+    e1.record(s)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    for p in plans:
+        p.check()
+    info = batch.info()
+    # each plan alone, for reference (own launches, own tuned shape)
+    alone = []
+    for p, y, o in zip(plans, ys, outs):
+        autotune.tune_plan(p, y, o, staging=(True,), reps=2)
+        t = autotune._time(lambda: p.forward(y, o), max(2, args.steps // 2), 1)
+        alone.append(y.shape[0] / (t * 1e-3))
+    actives = [p.count_active() for p in plans]
+    flops = sum(a * f * 16.0 for a, f in zip(actives, frames))
+    sm_max = float(measured_peaks()[0].get("sm_max_mhz", 2070.0))
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    line = {
+        "metric": "volumes/s, batched forward DAS over 3 uneven plans in one persistent launch (FP16 IQ storage)",
+        "value": total / (ms * 1e-3), "unit": "volumes/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f16 storage, f32 arithmetic", "data": "synthetic",
+        "config": {"workload": "batched_3plans_64frames",
+                   "plans": [dict(sc.describe(), frames=f) for sc, f in zip(scenes, frames)],
+                   "tuning": {k: tuned[k] for k in ("frames_per_thread", "ctas_per_sm")},
+                   "work_items": info["work_items"]},
+        "per_plan_volumes_per_s_in_batch": [f / (ms * 1e-3) for f in frames],
+        "per_plan_volumes_per_s_alone": alone,
+        "roofline": {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": flops / (ms * 1e-3) / 1e12 / fp32_peak, "traffic": None,
+                     "note": "whole graph time (relayouts + persistent kernel)"},
+        "gpu_launches": info["kernels_per_launch"] * args.steps, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    batch.close()
+    for p in plans:
+        p.close()
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
     import torch
 
     from paper_2606_13259_gb300 import Plan

@@ -199,6 +199,26 @@ int das_grad_c_static(das_plan_t *plan, const void *y_dev, const void *gx_dev, d
  * kernels' own float32 decisions.  Synchronous; result in *count_host. */
 int das_count_active(das_plan_t *plan, long long *count_host, das_stream_t stream);
 
+/* Batches (the batched form): several plans -- grids of uneven size, element
+ * and transmit counts, one sample type and storage -- and all their frames in
+ * one persistent kernel launch.  The CTAs of the persistent grid take
+ * (plan, frame chunk, voxel tile) items from an atomic work counter, heaviest
+ * plans first, and run the forward tile body with that plan's arguments.  The
+ * per-plan relayouts, the counter reset and the persistent launch are captured
+ * once into a CUDA graph and replayed; a call with other data pointers
+ * captures a new graph.  Up to 8 plans; frames[i] <= max_batch of plan i.
+ * das_batch_create allocates the work list and may enlarge a plan's scratch;
+ * das_batch_forward allocates nothing after its first call.  A batch keeps
+ * pointers to its plans: destroy the batch first. */
+typedef struct das_batch das_batch_t;
+int das_batch_create(das_batch_t **out, das_plan_t *const *plans, const int *frames, int n_plans);
+/* y_dev[i]: [frames[i]][Q_i][M_i][K_i]; x_dev[i]: [frames[i]][N_i], overwritten. */
+int das_batch_forward(das_batch_t *batch, const void *const *y_dev, void *const *x_dev, das_stream_t stream);
+/* frames_per_thread and ctas_per_sm (persistent CTAs per SM, 0: as many as fit) */
+int das_batch_set_tuning(das_batch_t *batch, const das_tuning_t *tuning);
+int das_batch_info(const das_batch_t *batch, int *frames_per_thread, int *n_items, int *kernels_per_launch);
+void das_batch_destroy(das_batch_t *batch);
+
 /* Waits for the stream and reports kernel-side failures recorded since the
  * last check: DAS_ERR_TIMEOUT when a kernel gave up waiting for a staged copy
  * (it then left its outputs incomplete).  Clears the record. */

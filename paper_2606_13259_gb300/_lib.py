@@ -23,7 +23,8 @@ ERROR_NAMES = {DAS_ERR_INVALID_ARG: "invalid argument", DAS_ERR_CUDA: "CUDA erro
 EXPORTS = ["das_plan_create", "das_plan_destroy", "das_plan_set_c", "das_plan_info", "das_plan_set_tuning",
            "das_forward", "das_forward_host", "das_adjoint", "das_grad_c", "das_count_active",
            "das_plan_enable_timing", "das_plan_timing", "das_last_error", "das_version", "das_grad_c_static",
-           "das_plan_check"]
+           "das_plan_check", "das_batch_create", "das_batch_forward", "das_batch_set_tuning", "das_batch_info",
+           "das_batch_destroy"]
 
 
 class Geometry(C.Structure):
@@ -92,6 +93,16 @@ def lib():
         L.das_grad_c_static.restype = i
         L.das_count_active.argtypes = [vp, C.POINTER(C.c_longlong), vp]
         L.das_count_active.restype = i
+        L.das_batch_create.argtypes = [C.POINTER(vp), C.POINTER(vp), C.POINTER(C.c_int), i]
+        L.das_batch_create.restype = i
+        L.das_batch_forward.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), vp]
+        L.das_batch_forward.restype = i
+        L.das_batch_set_tuning.argtypes = [vp, C.POINTER(Tuning)]
+        L.das_batch_set_tuning.restype = i
+        L.das_batch_info.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.das_batch_info.restype = i
+        L.das_batch_destroy.argtypes = [vp]
+        L.das_batch_destroy.restype = None
         L.das_plan_check.argtypes = [vp, vp]
         L.das_plan_check.restype = i
         L.das_plan_enable_timing.argtypes = [vp, i]

@@ -1,0 +1,125 @@
+"""Autotuner for the launch shape of the forward kernels.
+
+Times every candidate (frames per thread, persistent CTAs per SM, staged or
+global sample windows) on the caller's own data with CUDA events, keeps the
+fastest and caches the choice in a JSON file keyed by the GPU name and a
+signature of the workload (grid, elements, transmits, samples, frames, data
+and storage types).  The cache lives at $DAS_TUNING_CACHE, else
+~/.cache/paper_2606_13259_gb300/tuning.json.
+"""
+from __future__ import annotations
+
+import json
+import os
+from typing import Iterable, Optional
+
+import torch
+
+from . import _lib as L
+from .plan import Batch, Plan
+
+F32_FB = (2, 4, 8, 12, 16, 20)
+F16_FB = (4, 8, 12, 16, 20, 24)
+
+
+def cache_path() -> str:
+    return os.environ.get("DAS_TUNING_CACHE") or os.path.join(
+        os.path.expanduser("~"), ".cache", "paper_2606_13259_gb300", "tuning.json")
+
+
+def _load() -> dict:
+    try:
+        with open(cache_path()) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(key: str, value: dict) -> None:
+    data = _load()
+    data[key] = value
+    path = cache_path()
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def _plan_sig(p: Plan) -> str:
+    return f"{p.shape[2]}x{p.shape[1]}x{p.shape[0]}/M{p.M}/Q{p.Q}/K{p.K}/{'iq' if p.iq else 'rf'}/{p.storage}"
+
+
+def _time(fn, reps: int, warmup: int) -> float:
+    for _ in range(warmup):
+        fn()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(reps):
+        fn()
+    e1.record(s)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def tune_batch(batch: Batch, ys, outs, fbs: Optional[Iterable[int]] = None,
+               ctas: Iterable[int] = (0, 1, 2, 3), reps: int = 3, warmup: int = 1,
+               use_cache: bool = True) -> dict:
+    """Pick (frames per thread, CTAs per SM) for a batch; applies and returns it."""
+    key = "batch:" + torch.cuda.get_device_name() + ":" + ";".join(
+        f"{_plan_sig(p)}/B{f}" for p, f in zip(batch.plans, batch.frames))
+    if use_cache:
+        hit = _load().get(key)
+        if hit:
+            batch.set_tuning(hit["frames_per_thread"], hit["ctas_per_sm"])
+            return dict(hit, cached=True)
+    p0 = batch.plans[0]
+    if fbs is None:
+        fbs = F32_FB if p0.storage == "f32" else F16_FB
+    results = []
+    for fb in fbs:
+        for c in ctas:
+            try:
+                batch.set_tuning(fb, c)
+            except L.DASError:
+                continue
+            ms = _time(lambda: batch.forward(ys, outs), reps, warmup)
+            results.append({"frames_per_thread": fb, "ctas_per_sm": c, "ms": ms})
+    best = min(results, key=lambda r: r["ms"])
+    batch.set_tuning(best["frames_per_thread"], best["ctas_per_sm"])
+    out = {"frames_per_thread": best["frames_per_thread"], "ctas_per_sm": best["ctas_per_sm"], "ms": best["ms"],
+           "candidates": results}
+    if use_cache:
+        _store(key, out)
+    return dict(out, cached=False)
+
+
+def tune_plan(plan: Plan, y, out, fbs: Optional[Iterable[int]] = None, staging=(True, False),
+              reps: int = 3, warmup: int = 1, use_cache: bool = True) -> dict:
+    """Pick (frames per thread, staged windows) for single-plan forward calls."""
+    B = y.shape[0]
+    key = "plan:" + torch.cuda.get_device_name() + ":" + _plan_sig(plan) + f"/B{B}"
+    if use_cache:
+        hit = _load().get(key)
+        if hit:
+            plan.set_tuning(hit["frames_per_thread"], 0, hit["staging"])
+            return dict(hit, cached=True)
+    if fbs is None:
+        fbs = [f for f in ((1,) + (F32_FB if plan.storage == "f32" else F16_FB)) if f <= max(B, 1) * 2]
+    results = []
+    for fb in fbs:
+        for st in staging:
+            try:
+                plan.set_tuning(fb, 0, st)
+            except L.DASError:
+                continue
+            ms = _time(lambda: plan.forward(y, out), reps, warmup)
+            results.append({"frames_per_thread": fb, "staging": st, "ms": ms})
+    best = min(results, key=lambda r: r["ms"])
+    plan.set_tuning(best["frames_per_thread"], 0, best["staging"])
+    res = {"frames_per_thread": best["frames_per_thread"], "staging": best["staging"], "ms": best["ms"],
+           "candidates": results}
+    if use_cache:
+        _store(key, res)
+    return dict(res, cached=False)

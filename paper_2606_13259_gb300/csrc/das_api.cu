@@ -101,8 +101,11 @@ int dalloc(das_plan *p, void **ptr, size_t bytes, const char *what) {
     return DAS_OK;
 }
 
+// Frees one of the plan's buffers after the device has finished all work that
+// may still read it.
 void dfree(das_plan *p, void *ptr) {
     if (!ptr) return;
+    cudaDeviceSynchronize();
     for (size_t i = 0; i < p->allocs.size(); ++i)
         if (p->allocs[i] == ptr) { p->allocs.erase(p->allocs.begin() + i); break; }
     cudaFree(ptr);
@@ -748,5 +751,229 @@ extern "C" int das_grad_c_static(das_plan_t *plan, const void *y_dev, const void
     DAS_CU(launch_tile(A, MODE_DC, is_iq(plan), DAS_STORE_F32, fb, nch, s));
     DAS_CU(launch_reduce(partial, np, dLdc_dev, s));
     plan->launches += 2;
+    return DAS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batches: several plans and all their frames in one persistent launch,
+// replayed from a CUDA graph.
+// ---------------------------------------------------------------------------
+
+#include "das_batch.cuh"
+
+struct das_batch {
+    int device = 0;
+    int n = 0;
+    das_plan *plans[BATCH_MAX_PLANS] = {nullptr};
+    int frames[BATCH_MAX_PLANS] = {0};
+    int fb = 0;
+    das_tuning_t tuning{0, 0, 0};
+    int4 *items = nullptr;
+    int n_items = 0;
+    int *counter = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const void *cap_y[BATCH_MAX_PLANS] = {nullptr};
+    void *cap_x[BATCH_MAX_PLANS] = {nullptr};
+    int kernels_per_launch = 0;
+    long long launches = 0;
+};
+
+namespace {
+
+void batch_drop_graph(das_batch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+}
+
+int batch_choose_fb(const das_batch *b) {
+    const das_plan *p = b->plans[0];
+    if (b->tuning.frames_per_thread > 0) return b->tuning.frames_per_thread;
+    static const int cands[] = {24, 20, 16, 12, 8, 4, 2};
+    int best = 0;
+    long best_cost = -1;
+    for (int fb : cands) {
+        if (!batch_fb_supported(is_iq(p), p->storage, fb)) continue;
+        long cost = 0;
+        for (int i = 0; i < b->n; ++i) cost += (long)((b->frames[i] + fb - 1) / fb) * (6 + fb);
+        if (best_cost < 0 || cost < best_cost) { best_cost = cost; best = fb; }
+    }
+    return best;
+}
+
+// Scratch of plan p for `bs` padded frames, enlarged if needed.
+int ensure_scratch_frames(das_plan *p, int bs) {
+    const size_t need = (size_t)p->Q * p->M * p->K * (size_t)bs * sample_bytes_store(p);
+    if (need <= p->z_bytes) return DAS_OK;
+    dfree(p, p->z);
+    p->bytes -= p->z_bytes;
+    p->z = nullptr;
+    p->z_bytes = 0;
+    int rc = dalloc(p, &p->z, need, "channel-data scratch");
+    if (rc == DAS_OK) p->z_bytes = need;
+    return rc;
+}
+
+// Work list: (plan, chunk, tile), the plans with the most work per tile first.
+int batch_build(das_batch *b) {
+    const int fb = batch_choose_fb(b);
+    if (!batch_fb_supported(is_iq(b->plans[0]), b->plans[0]->storage, fb))
+        return fail(DAS_ERR_UNSUPPORTED, "frames_per_thread %d not compiled for batches of this storage", fb);
+    int order[BATCH_MAX_PLANS];
+    for (int i = 0; i < b->n; ++i) order[i] = i;
+    for (int i = 0; i < b->n; ++i)
+        for (int j = i + 1; j < b->n; ++j) {
+            const das_plan *pi = b->plans[order[i]], *pj = b->plans[order[j]];
+            if ((long long)pj->M * pj->Q > (long long)pi->M * pi->Q) std::swap(order[i], order[j]);
+        }
+    std::vector<int4> items;
+    for (int oi = 0; oi < b->n; ++oi) {
+        const int i = order[oi];
+        das_plan *p = b->plans[i];
+        const int nch = (b->frames[i] + fb - 1) / fb;
+        int rc = ensure_scratch_frames(p, nch * fb);
+        if (rc != DAS_OK) return rc;
+        const long long T = n_tiles(p->g);
+        for (int c = 0; c < nch; ++c)
+            for (long long t = 0; t < T; ++t) items.push_back(make_int4(i, c, (int)t, 0));
+    }
+    if (items.size() > 0x7fffffff) return fail(DAS_ERR_UNSUPPORTED, "too many work items");
+    if (b->items) cudaFree(b->items);
+    b->items = nullptr;
+    DAS_CU(cudaMalloc(&b->items, sizeof(int4) * items.size()));
+    DAS_CU(cudaMemcpy(b->items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice));
+    b->n_items = (int)items.size();
+    b->fb = fb;
+    batch_drop_graph(b);
+    return DAS_OK;
+}
+
+}  // namespace
+
+extern "C" int das_batch_create(das_batch_t **out, das_plan_t *const *plans, const int *frames, int n_plans) {
+    g_err[0] = 0;
+    if (!out) return fail(DAS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!plans || !frames) return fail(DAS_ERR_INVALID_ARG, "NULL argument");
+    if (n_plans < 1 || n_plans > BATCH_MAX_PLANS)
+        return fail(DAS_ERR_UNSUPPORTED, "a batch holds 1..%d plans (got %d)", BATCH_MAX_PLANS, n_plans);
+    for (int i = 0; i < n_plans; ++i) {
+        if (!plans[i]) return fail(DAS_ERR_INVALID_ARG, "plan %d is NULL", i);
+        if (frames[i] < 1 || frames[i] > plans[i]->max_batch)
+            return fail(DAS_ERR_INVALID_ARG, "plan %d: frames %d outside 1..max_batch (%d)", i, frames[i],
+                        plans[i]->max_batch);
+        if (plans[i]->device != plans[0]->device || plans[i]->sample_type != plans[0]->sample_type ||
+            plans[i]->storage != plans[0]->storage)
+            return fail(DAS_ERR_INVALID_ARG, "plans of a batch share device, sample type and storage");
+        for (int j = 0; j < i; ++j)
+            if (plans[j] == plans[i]) return fail(DAS_ERR_INVALID_ARG, "plan %d appears twice", i);
+    }
+    das_batch *b = new (std::nothrow) das_batch();
+    if (!b) return fail(DAS_ERR_OOM, "host allocation failed");
+    b->n = n_plans;
+    b->device = plans[0]->device;
+    for (int i = 0; i < n_plans; ++i) { b->plans[i] = plans[i]; b->frames[i] = frames[i]; }
+    DeviceGuard guard(b->device);
+    int rc = DAS_OK;
+    cudaError_t e;
+    if ((e = cudaMalloc(&b->counter, sizeof(int))) != cudaSuccess) rc = cuda_fail(e, "cudaMalloc(counter)");
+    else if ((e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking)) != cudaSuccess) rc = cuda_fail(e, "cudaStreamCreate");
+    else rc = batch_build(b);
+    if (rc != DAS_OK) {
+        if (b->items) cudaFree(b->items);
+        if (b->counter) cudaFree(b->counter);
+        if (b->cap) cudaStreamDestroy(b->cap);
+        delete b;
+        return rc;
+    }
+    *out = b;
+    return DAS_OK;
+}
+
+extern "C" void das_batch_destroy(das_batch_t *b) {
+    if (!b) return;
+    DeviceGuard guard(b->device);
+    cudaDeviceSynchronize();
+    batch_drop_graph(b);
+    if (b->items) cudaFree(b->items);
+    if (b->counter) cudaFree(b->counter);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
+}
+
+extern "C" int das_batch_set_tuning(das_batch_t *b, const das_tuning_t *tuning) {
+    if (!b || !tuning) return fail(DAS_ERR_INVALID_ARG, "NULL argument");
+    if (tuning->frames_per_thread < 0 || tuning->ctas_per_sm < 0 || tuning->no_staging < 0)
+        return fail(DAS_ERR_INVALID_ARG, "negative tuning value");
+    if (tuning->no_staging) return fail(DAS_ERR_UNSUPPORTED, "batches always stage sample windows");
+    DeviceGuard guard(b->device);
+    b->tuning = *tuning;
+    return batch_build(b);
+}
+
+extern "C" int das_batch_info(const das_batch_t *b, int *frames_per_thread, int *n_items, int *kernels_per_launch) {
+    if (!b) return fail(DAS_ERR_INVALID_ARG, "batch is NULL");
+    if (frames_per_thread) *frames_per_thread = b->fb;
+    if (n_items) *n_items = b->n_items;
+    if (kernels_per_launch) *kernels_per_launch = b->kernels_per_launch;
+    return DAS_OK;
+}
+
+extern "C" int das_batch_forward(das_batch_t *b, const void *const *y_dev, void *const *x_dev, das_stream_t stream) {
+    g_err[0] = 0;
+    if (!b || !y_dev || !x_dev) return fail(DAS_ERR_INVALID_ARG, "NULL argument");
+    for (int i = 0; i < b->n; ++i) {
+        const size_t al = is_iq(b->plans[i]) ? 8 : 4;
+        if (!y_dev[i] || !x_dev[i] || !aligned(y_dev[i], al) || !aligned(x_dev[i], al))
+            return fail(DAS_ERR_INVALID_ARG, "plan %d: NULL or misaligned data pointer", i);
+    }
+    DeviceGuard guard(b->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc;
+    for (int i = 0; i < b->n; ++i)
+        if ((rc = prepare_if_dirty(b->plans[i], s)) != DAS_OK) return rc;
+    bool same = b->exec != nullptr;
+    for (int i = 0; i < b->n && same; ++i) same = (b->cap_y[i] == y_dev[i] && b->cap_x[i] == x_dev[i]);
+    if (!same) {
+        batch_drop_graph(b);
+        BatchParams P{};
+        DAS_CU(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+        int kernels = 0;
+        for (int i = 0; i < b->n && rc == DAS_OK; ++i) {
+            das_plan *p = b->plans[i];
+            const int nch = (b->frames[i] + b->fb - 1) / b->fb;
+            const long long l0 = p->launches;
+            const void *z = nullptr;
+            rc = stage_channels(p, y_dev[i], b->frames[i], b->fb, nch, b->cap, &z);
+            kernels += (int)(p->launches - l0);
+            P.plans[i] = tile_args(p, b->frames[i], b->fb, z);
+            P.plans[i].x = x_dev[i];
+            if (P.plans[i].umax <= 0) P.plans[i].umax = window_rows((p->fs / p->c) * (double)P.plans[i].tile_radius);
+        }
+        cudaError_t e = cudaSuccess;
+        if (rc == DAS_OK) {
+            P.items = b->items;
+            P.n_items = b->n_items;
+            P.counter = b->counter;
+            e = cudaMemsetAsync(b->counter, 0, sizeof(int), b->cap);
+            if (e == cudaSuccess)
+                e = launch_batch(P, b->n, is_iq(b->plans[0]), b->plans[0]->storage, b->fb, b->tuning.ctas_per_sm, b->cap);
+            kernels += 1;
+        }
+        cudaGraph_t graph = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(b->cap, &graph);
+        if (rc != DAS_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
+        if (e != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return cuda_fail(e, "batch launch capture"); }
+        if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+        b->graph = graph;
+        DAS_CU(cudaGraphInstantiate(&b->exec, b->graph, 0));
+        for (int i = 0; i < b->n; ++i) { b->cap_y[i] = y_dev[i]; b->cap_x[i] = x_dev[i]; }
+        b->kernels_per_launch = kernels;
+    }
+    DAS_CU(cudaGraphLaunch(b->exec, s));
+    b->launches += b->kernels_per_launch;
     return DAS_OK;
 }

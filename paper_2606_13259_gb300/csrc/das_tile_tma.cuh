@@ -7,7 +7,10 @@
 // the rows any voxel of the tile can need form one contiguous window of
 // `umax` rows of z[chunk][q][m][.][FB]; thread 0 brings it into shared memory
 // with a single bulk asynchronous copy (cp.async.bulk, completion counted on
-// an mbarrier), TMA_STAGES items ahead of the consumers.  Threads then read
+// an mbarrier), up to TMA_STAGES items ahead of the consumers; a stage is
+// refilled once each of the four warps has arrived on the stage's "empty"
+// mbarrier, so warps drift apart by up to TMA_STAGES items instead of meeting
+// at a CTA-wide barrier for every item.  Threads then read
 // their two rows from shared memory, where lanes of a quarter-warp that need
 // up to four different rows do not conflict, instead of from L1, where every
 // distinct line costs a separate data-return wavefront.
@@ -27,7 +30,7 @@
 
 namespace das {
 
-constexpr int TMA_STAGES = 4;
+constexpr int TMA_STAGES = 6;
 constexpr uint32_t TMA_WAIT_LIMIT = 1u << 22;
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
@@ -97,19 +100,24 @@ __device__ __forceinline__ void item_window(int tb, int rb, float rf, float tmin
     cnt = max(kend - ks, 0);
 }
 
+// One (tile, frame chunk) of one plan; `smem` is the CTA's dynamic shared
+// memory (tile_tma_smem_bytes).  Returns false when a bounded wait expired.
+// Called by tile_tma_kernel (one launch per plan) and by the persistent
+// batch kernel (many plans, one launch).
 template <int FB, bool IQ, int ST, int MODE>
-__global__ void __launch_bounds__(TILE_N, TileOcc<FB>::v) tile_tma_kernel(const TileArgs A) {
+__device__ __forceinline__ bool tile_tma_body(const TileArgs &A, const long long tile, const int chunk,
+                                              unsigned char *smem, const unsigned grid_x) {
     using Row = FrameRow<FB, IQ, ST>;
     constexpr int SZ = Row::SZ;
     constexpr int RB = FB * SZ;  // bytes per staged row
     static_assert(RB % 16 == 0, "staged rows must be whole 16-byte vectors");
-    extern __shared__ __align__(16) unsigned char smem[];
     const int Q = A.Q;
     const int umax = A.umax;
     const bool has_w = A.w_tx != nullptr;
     unsigned char *stages = smem;                                                        // [S][umax][RB]
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(stages + (size_t)TMA_STAGES * umax * RB);  // [S]
-    float4 *s_eg = reinterpret_cast<float4 *>(mbar + TMA_STAGES);                       // [128]
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(stages + (size_t)TMA_STAGES * umax * RB);  // [S] full
+    uint64_t *ebar = mbar + TMA_STAGES;                                                  // [S] empty
+    float4 *s_eg = reinterpret_cast<float4 *>(ebar + TMA_STAGES);                       // [128]
     float4 *s_en = s_eg + TILE_N;                                                        // [128]
     float *s_t = reinterpret_cast<float *>(s_en + TILE_N);                              // [Q][128]
     float *s_w = s_t + Q * TILE_N;                                                       // [Q][128]
@@ -121,8 +129,7 @@ __global__ void __launch_bounds__(TILE_N, TileOcc<FB>::v) tile_tma_kernel(const 
     int *s_abort = s_cnt + 4;                                                            // [1]
 
     const int tid = threadIdx.x;
-    const long long tile = blockIdx.x;
-    const int b0 = blockIdx.y * FB;
+    const int b0 = chunk * FB;
     const GridDesc &g = A.g;
     const int tx = (int)(tile % g.tiles_x);
     const int ty = (int)((tile / g.tiles_x) % g.tiles_y);
@@ -139,9 +146,10 @@ __global__ void __launch_bounds__(TILE_N, TileOcc<FB>::v) tile_tma_kernel(const 
     const float dz = (float)(g.sz * (lz - 0.5 * (TILE_Z - 1)));
     const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     const unsigned char *zc = reinterpret_cast<const unsigned char *>(A.z) +
-                              (size_t)blockIdx.y * Q * A.M * A.K * (size_t)RB;  // this chunk
+                              (size_t)chunk * Q * A.M * A.K * (size_t)RB;  // this chunk
     const size_t qstride = (size_t)A.M * A.K * RB;
 
+    __syncthreads();  // a previous body call on this CTA is done with shared memory and barriers
     for (int q = 0; q < Q; ++q) {
         s_t[q * TILE_N + tid] = A.tx_t[(tile * Q + q) * TILE_N + tid];
         if (has_w) s_w[q * TILE_N + tid] = A.w_tx[(tile * Q + q) * TILE_N + tid];
@@ -151,7 +159,10 @@ __global__ void __launch_bounds__(TILE_N, TileOcc<FB>::v) tile_tma_kernel(const 
         s_tmin[q] = A.tx_tmin[tile * Q + q];
     }
     if (tid == 0) {
-        for (int s = 0; s < TMA_STAGES; ++s) mbar_init(&mbar[s], 1);
+        for (int s = 0; s < TMA_STAGES; ++s) {
+            mbar_init(&mbar[s], 1);               // completes when the copy has landed
+            mbar_init(&ebar[s], TILE_N / 32);     // completes when every warp is done with the stage
+        }
         mbar_init_fence();
         *s_abort = 0;
     }
@@ -161,10 +172,15 @@ __global__ void __launch_bounds__(TILE_N, TileOcc<FB>::v) tile_tma_kernel(const 
     for (int b = 0; b < FB; ++b) acc_r[b] = acc_i[b] = 0.f;
 
     // Thread 0 stages item i (element j = i / Q, transmit q = i % Q) of the
-    // current element block into stage (g0 + i) % S.
-    auto issue = [&](long long g0, int i) {
+    // current element block into stage (g0 + i) % S, once every warp is done
+    // with that stage's previous item.  Returns false if that wait expired.
+    int n_issued = 0;  // thread 0: items of the current element block issued so far
+    auto issue = [&](long long g0, int i) -> bool {
         const int j = i / Q, q = i - j * Q;
         const long long gi = g0 + i;
+        if (gi >= TMA_STAGES &&
+            !mbar_wait_bounded(&ebar[gi % TMA_STAGES], (uint32_t)(((gi / TMA_STAGES) - 1) & 1)))
+            return false;
         uint64_t *bar = &mbar[gi % TMA_STAGES];
         int ks, cnt;
         item_window(s_tb[q], s_erb[j], s_en[j].w, s_tmin[q], A.win_lo, umax, A.K, ks, cnt);
@@ -176,6 +192,8 @@ __global__ void __launch_bounds__(TILE_N, TileOcc<FB>::v) tile_tma_kernel(const 
         } else {
             mbar_arrive(bar);
         }
+        ++n_issued;
+        return true;
     };
 
     const int lane = tid & 31, warp = tid >> 5;
@@ -224,8 +242,11 @@ __global__ void __launch_bounds__(TILE_N, TileOcc<FB>::v) tile_tma_kernel(const 
         __syncthreads();
 
         const int n_items = total * Q;
+        volatile int *abort_flag = s_abort;
+        n_issued = 0;
         if (tid == 0)
-            for (int i = 0; i < TMA_STAGES && i < n_items; ++i) issue(g0, i);
+            for (int i = 0; i < TMA_STAGES && i < n_items; ++i)
+                if (!issue(g0, i)) { atomicOr(A.err, 1); *abort_flag = 1; break; }
 
         int j = 0, q = 0;
         bool inside = false;
@@ -254,9 +275,12 @@ __global__ void __launch_bounds__(TILE_N, TileOcc<FB>::v) tile_tma_kernel(const 
             }
             const long long gi = g0 + i;
             const int st = (int)(gi % TMA_STAGES);
-            if (!mbar_wait_bounded(&mbar[st], (uint32_t)((gi / TMA_STAGES) & 1))) {
-                atomicOr(A.err, 1);
-                *s_abort = 1;
+            if (*abort_flag) break;  // warp-uniform: one shared word, read by the whole warp
+            const bool timed_out = !mbar_wait_bounded(&mbar[st], (uint32_t)((gi / TMA_STAGES) & 1));
+            if (__any_sync(0xffffffffu, timed_out)) {
+                if (lane == 0) atomicOr(A.err, 1);
+                *abort_flag = 1;
+                break;
             }
             const float f = r + s_t[q * TILE_N + tid];
             const float fl = floorf(f);
@@ -294,52 +318,74 @@ __global__ void __launch_bounds__(TILE_N, TileOcc<FB>::v) tile_tma_kernel(const 
                 int ks, cnt;
                 item_window(s_tb[q], Rb, Nn.w, s_tmin[q], A.win_lo, umax, A.K, ks, cnt);
                 const int u = k - ks;
-                uint32_t w0[Row::NW], w1[Row::NW];
                 if (u >= 0 && u + 1 < cnt) {
+                    // rows u and u+1 of the staged window, FG frames at a time
+                    constexpr int FG = (FB % 4 == 0 && RB / FB * 4 % 16 == 0) ? 4 : FB;
+                    constexpr int GW = FG * SZ / 4;  // 32-bit words per group and row
                     const uint32_t a0 = smem_addr(stages) + (uint32_t)((st * umax + u) * RB);
 #pragma unroll
-                    for (int v = 0; v < Row::NW / 4; ++v) {
-                        const uint4 x0 = lds128(a0 + 16 * v), x1 = lds128(a0 + RB + 16 * v);
-                        w0[4 * v] = x0.x; w0[4 * v + 1] = x0.y; w0[4 * v + 2] = x0.z; w0[4 * v + 3] = x0.w;
-                        w1[4 * v] = x1.x; w1[4 * v + 1] = x1.y; w1[4 * v + 2] = x1.z; w1[4 * v + 3] = x1.w;
+                    for (int bg = 0; bg < FB; bg += FG) {
+                        uint32_t w0[GW], w1[GW];
+#pragma unroll
+                        for (int v = 0; v < GW / 4; ++v) {
+                            const uint4 x0 = lds128(a0 + bg * SZ + 16 * v), x1 = lds128(a0 + RB + bg * SZ + 16 * v);
+                            w0[4 * v] = x0.x; w0[4 * v + 1] = x0.y; w0[4 * v + 2] = x0.z; w0[4 * v + 3] = x0.w;
+                            w1[4 * v] = x1.x; w1[4 * v + 1] = x1.y; w1[4 * v + 2] = x1.z; w1[4 * v + 3] = x1.w;
+                        }
+                        using RowG = FrameRow<FG, IQ, ST>;
+#pragma unroll
+                        for (int b = 0; b < FG; ++b) {
+                            const float2 z0 = RowG::get(w0, b), z1 = RowG::get(w1, b);
+                            if constexpr (IQ) {
+                                acc_r[bg + b] = fmaf(c0r, z0.x, fmaf(-c0i, z0.y, fmaf(c1r, z1.x, fmaf(-c1i, z1.y, acc_r[bg + b]))));
+                                acc_i[bg + b] = fmaf(c0r, z0.y, fmaf(c0i, z0.x, fmaf(c1r, z1.y, fmaf(c1i, z1.x, acc_i[bg + b]))));
+                            } else {
+                                acc_r[bg + b] = fmaf(c0r, z0.x, fmaf(c1r, z1.x, acc_r[bg + b]));
+                            }
+                        }
                     }
                 } else {
+                    uint32_t w0[Row::NW], w1[Row::NW];
                     const unsigned char *p0 = zc + q * qstride + ((size_t)mm * A.K + k) * RB;
                     Row::load(p0, w0);
                     Row::load(p0 + RB, w1);
-                }
 #pragma unroll
-                for (int b = 0; b < FB; ++b) {
-                    const float2 z0 = Row::get(w0, b), z1 = Row::get(w1, b);
-                    if constexpr (IQ) {
-                        acc_r[b] = fmaf(c0r, z0.x, fmaf(-c0i, z0.y, fmaf(c1r, z1.x, fmaf(-c1i, z1.y, acc_r[b]))));
-                        acc_i[b] = fmaf(c0r, z0.y, fmaf(c0i, z0.x, fmaf(c1r, z1.y, fmaf(c1i, z1.x, acc_i[b]))));
-                    } else {
-                        acc_r[b] = fmaf(c0r, z0.x, fmaf(c1r, z1.x, acc_r[b]));
+                    for (int b = 0; b < FB; ++b) {
+                        const float2 z0 = Row::get(w0, b), z1 = Row::get(w1, b);
+                        if constexpr (IQ) {
+                            acc_r[b] = fmaf(c0r, z0.x, fmaf(-c0i, z0.y, fmaf(c1r, z1.x, fmaf(-c1i, z1.y, acc_r[b]))));
+                            acc_i[b] = fmaf(c0r, z0.y, fmaf(c0i, z0.x, fmaf(c1r, z1.y, fmaf(c1i, z1.x, acc_i[b]))));
+                        } else {
+                            acc_r[b] = fmaf(c0r, z0.x, fmaf(c1r, z1.x, acc_r[b]));
+                        }
                     }
                 }
             }
-            __syncthreads();  // stage st is free again
-            if (*s_abort) {
-                aborted = true;
-                if (tid == 0) {
-                    // copies that may still be in flight: items i .. i+S-1 were issued
-                    for (int d = 0; d < TMA_STAGES && i + d < n_items; ++d) {
-                        const long long gd = gi + d;
-                        mbar_wait_bounded(&mbar[gd % TMA_STAGES], (uint32_t)((gd / TMA_STAGES) & 1));
-                    }
-                }
-                break;
-            }
-            if (tid == 0 && i + TMA_STAGES < n_items) issue(g0, i + TMA_STAGES);
+            // this warp is done with stage st
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ebar[st]);
+            if (tid == 0 && i + TMA_STAGES < n_items && !*abort_flag)
+                if (!issue(g0, i + TMA_STAGES)) { atomicOr(A.err, 1); *abort_flag = 1; }
             if (++q == Q) {
                 q = 0;
                 ++j;
             }
         }
+        __syncthreads();
+        if (*abort_flag) {
+            aborted = true;
+            if (tid == 0) {
+                // copies that can still be in flight: the last S items issued (every
+                // earlier one was waited for through its stage's empty barrier)
+                for (int d = n_issued - 1; d >= 0 && d >= n_issued - TMA_STAGES; --d) {
+                    const long long gd = g0 + d;
+                    mbar_wait_bounded(&mbar[gd % TMA_STAGES], (uint32_t)((gd / TMA_STAGES) & 1));
+                }
+            }
+        }
         g0 += n_items;
     }
-    if (aborted) return;
+    if (aborted) return false;
 
     if constexpr (MODE == MODE_FWD) {
         if (valid) {
@@ -368,20 +414,30 @@ __global__ void __launch_bounds__(TILE_N, TileOcc<FB>::v) tile_tma_kernel(const 
                 }
             }
         }
-        __shared__ double red[TILE_N / 32];
+        double *red = reinterpret_cast<double *>(s_eg);  // element records are no longer read
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == 0) red[warp] = v;
         __syncthreads();
         if (tid == 0) {
             double s = 0.0;
             for (int w = 0; w < TILE_N / 32; ++w) s += red[w];
-            A.partial[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = s;
+            A.partial[(size_t)chunk * grid_x + tile] = s;
         }
     }
+    return true;
+}
+
+// Resident CTAs per SM asked of the compiler (register budget 65536 / (128 x v)).
+template <int FB> struct TmaOcc { static constexpr int v = FB <= 8 ? 6 : FB <= 12 ? 5 : 4; };
+
+template <int FB, bool IQ, int ST, int MODE>
+__global__ void __launch_bounds__(TILE_N, TmaOcc<FB>::v) tile_tma_kernel(const TileArgs A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    tile_tma_body<FB, IQ, ST, MODE>(A, blockIdx.x, blockIdx.y, smem, gridDim.x);
 }
 
 inline size_t tile_tma_smem_bytes(int Q, bool has_w, int umax, int rb) {
-    return (size_t)TMA_STAGES * umax * rb + sizeof(uint64_t) * TMA_STAGES + sizeof(float4) * 2 * TILE_N +
+    return (size_t)TMA_STAGES * umax * rb + sizeof(uint64_t) * 2 * TMA_STAGES + sizeof(float4) * 2 * TILE_N +
            sizeof(float) * ((size_t)Q * TILE_N * (has_w ? 2 : 1) + Q) + sizeof(int) * (2 * TILE_N + Q + 5);
 }
 

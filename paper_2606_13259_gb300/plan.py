@@ -242,3 +242,53 @@ class DASFunction(torch.autograd.Function):
 def das(y: torch.Tensor, c: torch.Tensor, plan: Plan) -> torch.Tensor:
     """Differentiable delay-and-sum: image of y at speed of sound c."""
     return DASFunction.apply(y, c, plan)
+
+
+class Batch:
+    """Several plans and all their frames in one persistent launch replayed
+    from a CUDA graph (das_batch_* in the C-ABI)."""
+
+    def __init__(self, plans, frames):
+        if len(plans) != len(frames):
+            raise ValueError("one frame count per plan")
+        self._lib = L.lib()
+        self.plans = list(plans)
+        self.frames = [int(f) for f in frames]
+        arr = (C.c_void_p * len(plans))(*[p._h.value for p in plans])
+        fr = (C.c_int * len(plans))(*self.frames)
+        h = C.c_void_p()
+        L.check(self._lib.das_batch_create(C.byref(h), arr, fr, len(plans)))
+        self._h = h
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self._lib.das_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_tuning(self, frames_per_thread: int = 0, ctas_per_sm: int = 0) -> None:
+        t = L.Tuning(int(frames_per_thread), int(ctas_per_sm), 0)
+        L.check(self._lib.das_batch_set_tuning(self._h, C.byref(t)))
+
+    def info(self) -> dict:
+        fb, n, k = C.c_int(), C.c_int(), C.c_int()
+        L.check(self._lib.das_batch_info(self._h, C.byref(fb), C.byref(n), C.byref(k)))
+        return {"frames_per_thread": fb.value, "work_items": n.value, "kernels_per_launch": k.value}
+
+    def forward(self, ys, outs=None, stream=None):
+        """ys[i]: (frames[i], Q_i, M_i, K_i) -> images [(frames[i], nz, ny, nx)]."""
+        if outs is None:
+            outs = [torch.empty((f,) + p.shape, dtype=p.data_dtype, device=p.device)
+                    for p, f in zip(self.plans, self.frames)]
+        for p, f, y, o in zip(self.plans, self.frames, ys, outs):
+            if p._check(y, (p.Q, p.M, p.K), "y") != f or p._check(o, p.shape, "out") != f:
+                raise ValueError("batch sizes differ from the frame counts of the batch")
+        yp = (C.c_void_p * len(ys))(*[y.data_ptr() for y in ys])
+        xp = (C.c_void_p * len(outs))(*[o.data_ptr() for o in outs])
+        L.check(self._lib.das_batch_forward(self._h, yp, xp, _stream(stream)))
+        return outs
