@@ -38,8 +38,9 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["paper", "batched"], default="paper",
-                    help="paper: the 128^3 x 1024 x 16 forward; batched: three uneven plans, 64 frames, one launch")
+    ap.add_argument("--workload", choices=["paper", "batched", "table1"], default="paper",
+                    help="paper: the 128^3 x 1024 x 16 forward; batched: three uneven plans, 64 frames, one "
+                         "launch; table1: the paper's Table 1 configuration (B 128, Q 1, K 256)")
     ap.add_argument("--frames", type=int, default=20)
     ap.add_argument("--K", type=int, default=2048, help="samples per channel (all delays lie below 400)")
     ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32")
@@ -298,12 +299,70 @@ def run_batched(args):
         p.close()
 
 
+def run_table1(args):
+    """The paper's Table 1 configuration: 128 frames, 32x32 elements at pitch
+    lambda, 128^3 voxels at lambda / 2, one observation, 256 IQ samples."""
+    import torch
+
+    from paper_2606_13259_gb300 import Plan
+    from paper_2606_13259_gb300 import build as B
+    from paper_2606_13259_gb300 import synth as S
+
+    torch.cuda.set_device(0)
+    B.build()
+    sc = S.scene_table1()
+    F = 128
+    y = S.frames(sc, F, seed=6, n_speckle=4000, points=S.paper_points(sc), device="cuda")
+    plan = Plan.from_scene(sc, storage=args.storage, max_batch=F)
+    if args.no_staging or args.fb:
+        plan.set_tuning(frames_per_thread=args.fb, staging=not args.no_staging)
+    out = torch.empty((F,) + plan.shape, dtype=torch.complex64, device="cuda")
+    active = plan.count_active()
+    for _ in range(args.warmup):
+        plan.forward(y, out)
+    torch.cuda.synchronize()
+    plan.enable_timing(args.steps)
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.3)
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(args.steps):
+        plan.forward(y, out)
+    e1.record(s)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    plan.check()
+    ms = e0.elapsed_time(e1) / args.steps
+    kms, kn = plan.timing()
+    kern_ms = kms / max(kn, 1)
+    sm_max = float(measured_peaks()[0].get("sm_max_mhz", 2070.0))
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    flops = active * F * 16.0
+    line = {
+        "metric": "volumes/s, forward DAS in the paper's Table 1 configuration (B 128, M 1024, Q 1, K 256, N 128^3)",
+        "value": F / (ms * 1e-3), "unit": "volumes/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": args.storage + " storage, f32 arithmetic", "data": "synthetic",
+        "config": {"workload": sc.name, "frames_per_step": F, "scene": sc.describe()},
+        "roofline": {"bound": "alu", "achieved": flops / (kern_ms * 1e-3) / 1e12, "peak": fp32_peak,
+                     "unit": "TFLOP/s", "frac": flops / (kern_ms * 1e-3) / 1e12 / fp32_peak, "traffic": None,
+                     "kernel_ms": kern_ms},
+        "gpu_launches": None, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    plan.close()
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "table1":
+        return run_table1(args)
     import torch
 
     from paper_2606_13259_gb300 import Plan

@@ -30,7 +30,7 @@
 
 namespace das {
 
-constexpr int TMA_STAGES = 6;
+constexpr int TMA_STAGES = 10;
 constexpr uint32_t TMA_WAIT_LIMIT = 1u << 22;
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
@@ -117,7 +117,8 @@ __device__ __forceinline__ bool tile_tma_body(const TileArgs &A, const long long
     unsigned char *stages = smem;                                                        // [S][umax][RB]
     uint64_t *mbar = reinterpret_cast<uint64_t *>(stages + (size_t)TMA_STAGES * umax * RB);  // [S] full
     uint64_t *ebar = mbar + TMA_STAGES;                                                  // [S] empty
-    float4 *s_eg = reinterpret_cast<float4 *>(ebar + TMA_STAGES);                       // [128]
+    int2 *s_win = reinterpret_cast<int2 *>(ebar + TMA_STAGES);                          // [S] (first row, rows)
+    float4 *s_eg = reinterpret_cast<float4 *>(s_win + TMA_STAGES + (TMA_STAGES & 1));  // [128]
     float4 *s_en = s_eg + TILE_N;                                                        // [128]
     float *s_t = reinterpret_cast<float *>(s_en + TILE_N);                              // [Q][128]
     float *s_w = s_t + Q * TILE_N;                                                       // [Q][128]
@@ -184,6 +185,7 @@ __device__ __forceinline__ bool tile_tma_body(const TileArgs &A, const long long
         uint64_t *bar = &mbar[gi % TMA_STAGES];
         int ks, cnt;
         item_window(s_tb[q], s_erb[j], s_en[j].w, s_tmin[q], A.win_lo, umax, A.K, ks, cnt);
+        s_win[gi % TMA_STAGES] = make_int2(ks, cnt);  // published to the consumers by the arrive below
         if (cnt > 0) {
             const uint32_t bytes = (uint32_t)cnt * RB;
             mbar_arrive_expect_tx(bar, bytes);
@@ -315,10 +317,9 @@ __device__ __forceinline__ bool tile_tma_body(const TileArgs &A, const long long
                         c1r = s;
                     }
                 }
-                int ks, cnt;
-                item_window(s_tb[q], Rb, Nn.w, s_tmin[q], A.win_lo, umax, A.K, ks, cnt);
-                const int u = k - ks;
-                if (u >= 0 && u + 1 < cnt) {
+                const int2 win = s_win[st];
+                const int u = k - win.x;
+                if (u >= 0 && u + 1 < win.y) {
                     // rows u and u+1 of the staged window, FG frames at a time
                     constexpr int FG = (FB % 4 == 0 && RB / FB * 4 % 16 == 0) ? 4 : FB;
                     constexpr int GW = FG * SZ / 4;  // 32-bit words per group and row
@@ -364,8 +365,9 @@ __device__ __forceinline__ bool tile_tma_body(const TileArgs &A, const long long
             // this warp is done with stage st
             __syncwarp();
             if (lane == 0) mbar_arrive(&ebar[st]);
-            if (tid == 0 && i + TMA_STAGES < n_items && !*abort_flag)
-                if (!issue(g0, i + TMA_STAGES)) { atomicOr(A.err, 1); *abort_flag = 1; }
+            // refill the stage of the previous item (one item of slack for the other warps)
+            if (tid == 0 && i >= 1 && i - 1 + TMA_STAGES < n_items && !*abort_flag)
+                if (!issue(g0, i - 1 + TMA_STAGES)) { atomicOr(A.err, 1); *abort_flag = 1; }
             if (++q == Q) {
                 q = 0;
                 ++j;
@@ -437,7 +439,8 @@ __global__ void __launch_bounds__(TILE_N, TmaOcc<FB>::v) tile_tma_kernel(const T
 }
 
 inline size_t tile_tma_smem_bytes(int Q, bool has_w, int umax, int rb) {
-    return (size_t)TMA_STAGES * umax * rb + sizeof(uint64_t) * 2 * TMA_STAGES + sizeof(float4) * 2 * TILE_N +
+    return (size_t)TMA_STAGES * umax * rb + sizeof(uint64_t) * 2 * TMA_STAGES +
+           sizeof(int2) * (TMA_STAGES + (TMA_STAGES & 1)) + sizeof(float4) * 2 * TILE_N +
            sizeof(float) * ((size_t)Q * TILE_N * (has_w ? 2 : 1) + Q) + sizeof(int) * (2 * TILE_N + Q + 5);
 }
 

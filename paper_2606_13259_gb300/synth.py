@@ -177,6 +177,23 @@ def scenes_batched() -> list[Scene]:
     return [p1, p2, p3]
 
 
+def scene_table1(fc: float = 7.5e6, c: float = 1540.0) -> Scene:
+    """The evaluation configuration of the paper's Table 1: M = 32 x 32
+    elements at a pitch of one wavelength, N = 128^3 voxels at half a
+    wavelength, Q = 1 observation, K = 256 samples.  The table leaves the
+    transmit, the sampling rate and the depth open; here one plane wave at
+    normal incidence, IQ sampled at 2 fc (K = 256 then spans 128 wavelengths
+    of two-way path, the depth extent of the grid), first voxel half a
+    wavelength below the array, f-number 1."""
+    lam = c / fc
+    pos, nrm = matrix_array(32, 32, lam)
+    kind = np.array([TX_PLANE], dtype=np.int32)
+    vec = np.array([[0.0, 0.0, 1.0]])
+    return Scene("table1_iq_128cube_1024el_1tx", 128, 128, 128, centred_origin(128, 128, lam / 2, lam / 2, lam / 2),
+                 (lam / 2,) * 3, pos, nrm, kind, vec, c=c, fs=2 * fc, f_demod=fc, f_number=1.0, K=256, iq=True,
+                 fc=fc)
+
+
 def scene_tiny(iq: bool = True, n: tuple = (3, 3, 3), elems: tuple = (2, 2), n_tx: int = 2,
                K: int = 64, f_number: float = 0.0) -> Scene:
     """A few voxels and elements for brute-force checks (fs 30 MHz, 0.1 mm voxels from 1 mm depth)."""
