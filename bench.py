@@ -38,7 +38,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["paper", "batched", "table1"], default="paper",
+    ap.add_argument("--workload", choices=["paper", "batched", "table1", "diff"], default="paper",
                     help="paper: the 128^3 x 1024 x 16 forward; batched: three uneven plans, 64 frames, one "
                          "launch; table1: the paper's Table 1 configuration (B 128, Q 1, K 256)")
     ap.add_argument("--frames", type=int, default=20)
@@ -47,7 +47,8 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-staging", action="store_true", help="read sample rows from global memory (no TMA windows)")
+    ap.add_argument("--staging", action="store_true", help="stage sample windows in shared memory (bulk copies)")
+    ap.add_argument("--load-width", type=int, default=0, choices=[0, 128, 256], help="bits per lane of each load")
     ap.add_argument("--fb", type=int, default=0, help="frames per thread (0: automatic)")
     return ap.parse_args()
 
@@ -314,8 +315,8 @@ def run_table1(args):
     F = 128
     y = S.frames(sc, F, seed=6, n_speckle=4000, points=S.paper_points(sc), device="cuda")
     plan = Plan.from_scene(sc, storage=args.storage, max_batch=F)
-    if args.no_staging or args.fb:
-        plan.set_tuning(frames_per_thread=args.fb, staging=not args.no_staging)
+    if args.staging or args.fb or args.load_width:
+        plan.set_tuning(frames_per_thread=args.fb, staging=args.staging, load_width=args.load_width)
     out = torch.empty((F,) + plan.shape, dtype=torch.complex64, device="cuda")
     active = plan.count_active()
     for _ in range(args.warmup):
@@ -355,8 +356,67 @@ def run_table1(args):
     plan.close()
 
 
+def run_diff(args):
+    """Differentiation form: 96^3 voxels x 1024 elements x 8 transmits, IQ,
+    1536 samples, one frame.  A step is the forward pass, the adjoint of an
+    image-space cotangent and the sound-speed derivative (what a gradient
+    step of an autofocus loop costs)."""
+    import torch
+
+    from paper_2606_13259_gb300 import Plan
+    from paper_2606_13259_gb300 import build as B
+    from paper_2606_13259_gb300 import synth as S
+
+    torch.cuda.set_device(0)
+    B.build()
+    sc = S.scene_diff(c=1500.0)
+    y = S.frames(sc, 1, seed=5, n_speckle=20000, points=S.paper_points(sc), c=1540.0, device="cuda")
+    g = S.random_image(sc, 1, seed=12).cuda().reshape((1, sc.nz, sc.ny, sc.nx))
+    plan = Plan.from_scene(sc)
+    x = torch.empty((1,) + plan.shape, dtype=torch.complex64, device="cuda")
+    ya = torch.empty_like(y)
+    dc = torch.empty((), dtype=torch.float64, device="cuda")
+    s = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(s)
+        for _ in range(args.steps):
+            fn()
+        e1.record(s)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.3)
+    t_fwd = timed(lambda: plan.forward(y, x))
+    t_adj = timed(lambda: plan.adjoint(g, ya))
+    t_dc = timed(lambda: plan.grad_c(y, g, dc))
+    clocks = sampler.stop()
+    plan.check()
+    active = plan.count_active()
+    step = t_fwd + t_adj + t_dc
+    line = {
+        "metric": "differentiation steps/s (forward + adjoint + dL/dc) at 96^3 voxels x 1024 elements x 8 transmits",
+        "value": 1e3 / step, "unit": "steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": {"workload": sc.name, "frames": 1, "scene": sc.describe()},
+        "ms": {"forward": t_fwd, "adjoint": t_adj, "grad_c": t_dc},
+        "terms_per_ms": {"forward": active / t_fwd, "adjoint": active / t_adj, "grad_c": active / t_dc},
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    plan.close()
+
+
 def main():
     args = parse_args()
+    if args.workload == "diff":
+        return run_diff(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":
@@ -389,8 +449,8 @@ def main():
     sc, y = make_inputs(args.frames, rank, dev, args.K)
     F = args.frames
     plan = Plan.from_scene(sc, storage=args.storage, max_batch=F)
-    if args.no_staging or args.fb:
-        plan.set_tuning(frames_per_thread=args.fb, staging=not args.no_staging)
+    if args.staging or args.fb or args.load_width:
+        plan.set_tuning(frames_per_thread=args.fb, staging=args.staging, load_width=args.load_width)
     out = torch.empty((F,) + plan.shape, dtype=torch.complex64, device=dev)
     active = plan.count_active()
 
@@ -465,7 +525,8 @@ def main():
         "config": {"workload": sc.name, "frames_per_step": F, "voxels": sc.N, "elements": sc.M,
                    "transmits": sc.Q, "samples": sc.K, "storage": args.storage,
                    "l2": f"inputs {y.numel() * 8 / 1e9:.1f} GB > 129 MB L2, no flush", "per_rank_frames": F,
-                   "staging": not args.no_staging, "frames_per_thread": args.fb or "auto"},
+                   "staging": args.staging, "load_width": args.load_width or 128,
+                   "frames_per_thread": args.fb or "auto"},
         "accumulations_per_s": world * F * sc.N * sc.M * sc.Q / (ms * 1e-3),
         "contributing_terms_per_volume": active,
         "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,

@@ -124,8 +124,10 @@ typedef struct {
 typedef struct {
     int frames_per_thread; /* frames accumulated per thread in the forward kernel (0: automatic) */
     int ctas_per_sm;       /* occupancy hint for persistent launches (0: automatic) */
-    int no_staging;        /* 1: read sample rows straight from global memory instead of staging
-                              each (element, transmit) window in shared memory with bulk copies */
+    int staging;           /* 1: stage each (element, transmit) window of sample rows in shared
+                              memory with bulk asynchronous copies; 0: read rows straight from
+                              global memory (default) */
+    int load_width;        /* bits per lane of each global sample load: 128 (default) or 256 */
 } das_tuning_t;
 
 /* Build a plan (Sec. 2 problem statement: grid, receivers, observations, c).

@@ -53,7 +53,8 @@ class PlanInfo(C.Structure):
 
 
 class Tuning(C.Structure):
-    _fields_ = [("frames_per_thread", C.c_int), ("ctas_per_sm", C.c_int), ("no_staging", C.c_int)]
+    _fields_ = [("frames_per_thread", C.c_int), ("ctas_per_sm", C.c_int), ("staging", C.c_int),
+                ("load_width", C.c_int)]
 
 
 class DASError(RuntimeError):

@@ -95,31 +95,32 @@ def tune_batch(batch: Batch, ys, outs, fbs: Optional[Iterable[int]] = None,
     return dict(out, cached=False)
 
 
-def tune_plan(plan: Plan, y, out, fbs: Optional[Iterable[int]] = None, staging=(True, False),
-              reps: int = 3, warmup: int = 1, use_cache: bool = True) -> dict:
-    """Pick (frames per thread, staged windows) for single-plan forward calls."""
+def tune_plan(plan: Plan, y, out, fbs: Optional[Iterable[int]] = None, staging=(False, True),
+              load_widths=(128, 256), reps: int = 3, warmup: int = 1, use_cache: bool = True) -> dict:
+    """Pick (frames per thread, staged windows, load width) for single-plan forward calls."""
     B = y.shape[0]
     key = "plan:" + torch.cuda.get_device_name() + ":" + _plan_sig(plan) + f"/B{B}"
     if use_cache:
         hit = _load().get(key)
         if hit:
-            plan.set_tuning(hit["frames_per_thread"], 0, hit["staging"])
+            plan.set_tuning(hit["frames_per_thread"], 0, hit["staging"], hit.get("load_width", 0))
             return dict(hit, cached=True)
     if fbs is None:
         fbs = [f for f in ((1,) + (F32_FB if plan.storage == "f32" else F16_FB)) if f <= max(B, 1) * 2]
     results = []
     for fb in fbs:
         for st in staging:
-            try:
-                plan.set_tuning(fb, 0, st)
-            except L.DASError:
-                continue
-            ms = _time(lambda: plan.forward(y, out), reps, warmup)
-            results.append({"frames_per_thread": fb, "staging": st, "ms": ms})
+            for lw in (load_widths if not st else (128,)):
+                try:
+                    plan.set_tuning(fb, 0, st, lw)
+                except L.DASError:
+                    continue
+                ms = _time(lambda: plan.forward(y, out), reps, warmup)
+                results.append({"frames_per_thread": fb, "staging": st, "load_width": lw, "ms": ms})
     best = min(results, key=lambda r: r["ms"])
-    plan.set_tuning(best["frames_per_thread"], 0, best["staging"])
-    res = {"frames_per_thread": best["frames_per_thread"], "staging": best["staging"], "ms": best["ms"],
-           "candidates": results}
+    plan.set_tuning(best["frames_per_thread"], 0, best["staging"], best["load_width"])
+    res = {"frames_per_thread": best["frames_per_thread"], "staging": best["staging"],
+           "load_width": best["load_width"], "ms": best["ms"], "candidates": results}
     if use_cache:
         _store(key, res)
     return dict(res, cached=False)

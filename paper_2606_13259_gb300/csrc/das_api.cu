@@ -63,7 +63,7 @@ struct das_plan {
     void *stage_y = nullptr;
     void *stage_x = nullptr;
     bool dirty = true;
-    das_tuning_t tuning{0, 0, 0};
+    das_tuning_t tuning{0, 0, 0, 0};
     size_t bytes = 0;
     long long launches = 0;
     std::vector<cudaEvent_t> ev_start, ev_stop;
@@ -213,7 +213,8 @@ TileArgs tile_args(const das_plan *p, int B, int fb, const void *z) {
     A.fb = fb;
     fill_common(p, A.a, A.ad, A.theta, A.hr, A.hi, A.thr, A.tile_radius);
     const double aR = (p->fs / p->c) * (double)A.tile_radius;
-    A.umax = p->tuning.no_staging ? 0 : window_rows(aR);
+    A.umax = p->tuning.staging ? window_rows(aR) : 0;
+    A.w256 = p->tuning.load_width == 256 ? 1 : 0;
     A.win_lo = (float)(aR + 1e-3);
     A.tx_tmin = p->tx_tmin;
     A.err = p->err;
@@ -528,8 +529,10 @@ int das_plan_timing(das_plan_t *plan, double *ms_total, int *launches) {
 
 int das_plan_set_tuning(das_plan_t *plan, const das_tuning_t *tuning) {
     if (!plan || !tuning) return fail(DAS_ERR_INVALID_ARG, "NULL argument");
-    if (tuning->frames_per_thread < 0 || tuning->ctas_per_sm < 0 || tuning->no_staging < 0)
+    if (tuning->frames_per_thread < 0 || tuning->ctas_per_sm < 0 || tuning->staging < 0)
         return fail(DAS_ERR_INVALID_ARG, "negative tuning value");
+    if (tuning->load_width != 0 && tuning->load_width != 128 && tuning->load_width != 256)
+        return fail(DAS_ERR_INVALID_ARG, "load_width must be 0, 128 or 256");
     if (tuning->frames_per_thread > 0 &&
         !tile_fb_supported(MODE_FWD, is_iq(plan), plan->storage, tuning->frames_per_thread))
         return fail(DAS_ERR_UNSUPPORTED, "frames_per_thread %d not compiled for this storage", tuning->frames_per_thread);
@@ -767,7 +770,7 @@ struct das_batch {
     das_plan *plans[BATCH_MAX_PLANS] = {nullptr};
     int frames[BATCH_MAX_PLANS] = {0};
     int fb = 0;
-    das_tuning_t tuning{0, 0, 0};
+    das_tuning_t tuning{0, 0, 0, 0};
     int4 *items = nullptr;
     int n_items = 0;
     int *counter = nullptr;
@@ -906,9 +909,8 @@ extern "C" void das_batch_destroy(das_batch_t *b) {
 
 extern "C" int das_batch_set_tuning(das_batch_t *b, const das_tuning_t *tuning) {
     if (!b || !tuning) return fail(DAS_ERR_INVALID_ARG, "NULL argument");
-    if (tuning->frames_per_thread < 0 || tuning->ctas_per_sm < 0 || tuning->no_staging < 0)
+    if (tuning->frames_per_thread < 0 || tuning->ctas_per_sm < 0 || tuning->staging < 0)
         return fail(DAS_ERR_INVALID_ARG, "negative tuning value");
-    if (tuning->no_staging) return fail(DAS_ERR_UNSUPPORTED, "batches always stage sample windows");
     DeviceGuard guard(b->device);
     b->tuning = *tuning;
     return batch_build(b);

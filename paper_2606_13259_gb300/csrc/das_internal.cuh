@@ -77,7 +77,8 @@ struct TileArgs {
     int M, Q, K;
     int B;         // frames in this call
     int fb;        // frames per CTA chunk (= template FB) = samples per relayouted row
-    int umax;      // rows per staged sample window (TMA kernels)
+    int umax;      // rows per staged sample window (staged kernels); 0: rows come from global memory
+    int w256;      // 1: 256-bit global sample loads where rows allow
     float win_lo;  // a * tile radius + margin: lower reach of a window below the tile reference (samples)
     double ad;     // fs / c, float64
     float a;       // fs / c, float32

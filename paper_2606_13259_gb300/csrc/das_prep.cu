@@ -140,8 +140,10 @@ cudaError_t launch_scale(const void *y, float *scale, float *inv_scale, int iq, 
 // Batched: 32 frames x 32 samples per step through shared memory; reads are
 // contiguous along k, writes contiguous along the frames of a chunk.  The
 // output is chunk-major, z[c][qm][k][fb] holding frame b = c * fb + j, so the
-// rows one CTA of the tile kernels reads are contiguous.  Frames B .. Bs-1
-// (Bs = chunks * fb) are zero.
+// rows one CTA of the tile kernels reads are contiguous.  For IQ data and an
+// even fb a row is stored pair-planar (re_0, re_1, im_0, im_1, re_2, ...), so
+// the kernels can update two frames with one packed float32 FMA.  Frames
+// B .. Bs-1 (Bs = chunks * fb) are zero.
 template <bool IQ, int ST>
 __global__ void __launch_bounds__(256) relayout_kernel(const void *__restrict__ y_, void *__restrict__ z_,
                                                        const float2 *__restrict__ rot,
@@ -178,7 +180,14 @@ __global__ void __launch_bounds__(256) relayout_kernel(const void *__restrict__ 
                     if (rot) v = cmul(v, rot[k]);
                     v.x *= s;
                     v.y *= s;
-                    put(reinterpret_cast<OutC *>(z_) + o, v);
+                    if (fb % 2 == 0) {
+                        // pair-planar rows: re_{2p}, re_{2p+1}, im_{2p}, im_{2p+1}
+                        const size_t r = 2 * (o - j) + 4 * (j >> 1) + (j & 1);
+                        put(reinterpret_cast<OutR *>(z_) + r, v.x);
+                        put(reinterpret_cast<OutR *>(z_) + r + 2, v.y);
+                    } else {
+                        put(reinterpret_cast<OutC *>(z_) + o, v);
+                    }
                 } else {
                     put(reinterpret_cast<OutR *>(z_) + o, v.x * s);
                 }

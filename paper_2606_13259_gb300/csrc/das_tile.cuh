@@ -84,9 +84,133 @@ template <int FB, bool IQ, int ST> struct FrameRow {
     }
 };
 
+// 256-bit read-only global load (sm_100+), 32-byte aligned.
+__device__ __forceinline__ void ldg256(const void *p, uint32_t *w) {
+    asm volatile("ld.global.nc.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]), "=r"(w[7])
+                 : "l"(p));
+}
+
+// Row of FB samples with 256-bit loads where the row is whole 32-byte vectors.
+template <int FB, bool IQ, int ST, bool W256>
+__device__ __forceinline__ void load_row(const unsigned char *p, uint32_t (&w)[FrameRow<FB, IQ, ST>::NW]) {
+    using Row = FrameRow<FB, IQ, ST>;
+    if constexpr (W256 && !Row::HALFWORDS && Row::BYTES % 32 == 0) {
+#pragma unroll
+        for (int i = 0; i < Row::NW / 8; ++i) ldg256(p + 32 * i, &w[8 * i]);
+    } else {
+        Row::load(p, w);
+    }
+}
+
+// FB frame accumulators of one voxel.  With an even FB the rows are
+// pair-planar (IQ) or naturally paired (RF) and two frames are updated by one
+// packed float32 FMA (__ffma2_rn); with an odd FB the frames are updated one
+// by one from interleaved (re, im) samples.
+template <int FB, bool IQ, int ST> struct FrameAcc {
+    static constexpr bool PAIR = (FB % 2) == 0;
+    using Row = FrameRow<FB, IQ, ST>;
+    static constexpr int NP = PAIR ? FB / 2 : 1;
+    static constexpr int NS = PAIR ? 1 : FB;
+    float2 re2[NP], im2[NP];
+    float re1[NS], im1[NS];
+
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int p = 0; p < NP; ++p) re2[p] = im2[p] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int b = 0; b < NS; ++b) re1[b] = im1[b] = 0.f;
+    }
+
+    // (re, im) of frame pair p: two float2 holding frames 2p and 2p+1
+    __device__ __forceinline__ static void pair(const uint32_t *w, int p, float2 &re, float2 &im) {
+        if constexpr (IQ && ST == ST_F32) {
+            re = make_float2(__uint_as_float(w[4 * p]), __uint_as_float(w[4 * p + 1]));
+            im = make_float2(__uint_as_float(w[4 * p + 2]), __uint_as_float(w[4 * p + 3]));
+        } else if constexpr (IQ && ST == ST_F16) {
+            __half2 a, b;
+            *reinterpret_cast<uint32_t *>(&a) = w[2 * p];
+            *reinterpret_cast<uint32_t *>(&b) = w[2 * p + 1];
+            re = __half22float2(a);
+            im = __half22float2(b);
+        } else if constexpr (IQ && ST == ST_BF16) {
+            __nv_bfloat162 a, b;
+            *reinterpret_cast<uint32_t *>(&a) = w[2 * p];
+            *reinterpret_cast<uint32_t *>(&b) = w[2 * p + 1];
+            re = __bfloat1622float2(a);
+            im = __bfloat1622float2(b);
+        } else if constexpr (ST == ST_F32) {
+            re = make_float2(__uint_as_float(w[2 * p]), __uint_as_float(w[2 * p + 1]));
+        } else if constexpr (ST == ST_F16) {
+            __half2 a;
+            *reinterpret_cast<uint32_t *>(&a) = w[p];
+            re = __half22float2(a);
+        } else {
+            __nv_bfloat162 a;
+            *reinterpret_cast<uint32_t *>(&a) = w[p];
+            re = __bfloat1622float2(a);
+        }
+    }
+
+    // acc += c0 * tap0 + c1 * tap1 for frames [g0, g0 + G) of words w0, w1
+    // (w holds those frames only, starting at frame g0)
+    template <int G>
+    __device__ __forceinline__ void add(int g0, const uint32_t *w0, const uint32_t *w1, float c0r, float c0i,
+                                        float c1r, float c1i) {
+        if constexpr (PAIR) {
+            const float2 C0R = make_float2(c0r, c0r), C0I = make_float2(c0i, c0i);
+            const float2 N0I = make_float2(-c0i, -c0i), C1R = make_float2(c1r, c1r);
+            const float2 C1I = make_float2(c1i, c1i), N1I = make_float2(-c1i, -c1i);
+#pragma unroll
+            for (int p = 0; p < G / 2; ++p) {
+                float2 zr0, zi0, zr1, zi1;
+                pair(w0, p, zr0, zi0);
+                pair(w1, p, zr1, zi1);
+                const int q = g0 / 2 + p;
+                if constexpr (IQ) {
+                    re2[q] = __ffma2_rn(C0R, zr0, re2[q]);
+                    re2[q] = __ffma2_rn(N0I, zi0, re2[q]);
+                    re2[q] = __ffma2_rn(C1R, zr1, re2[q]);
+                    re2[q] = __ffma2_rn(N1I, zi1, re2[q]);
+                    im2[q] = __ffma2_rn(C0R, zi0, im2[q]);
+                    im2[q] = __ffma2_rn(C0I, zr0, im2[q]);
+                    im2[q] = __ffma2_rn(C1R, zi1, im2[q]);
+                    im2[q] = __ffma2_rn(C1I, zr1, im2[q]);
+                } else {
+                    re2[q] = __ffma2_rn(C0R, zr0, re2[q]);
+                    re2[q] = __ffma2_rn(C1R, zr1, re2[q]);
+                }
+            }
+        } else {
+            using RowG = FrameRow<G, IQ, ST>;
+#pragma unroll
+            for (int b = 0; b < G; ++b) {
+                const float2 z0 = RowG::get(*reinterpret_cast<const uint32_t(*)[RowG::NW]>(w0), b);
+                const float2 z1 = RowG::get(*reinterpret_cast<const uint32_t(*)[RowG::NW]>(w1), b);
+                const int f = g0 + b;
+                if constexpr (IQ) {
+                    re1[f] = fmaf(c0r, z0.x, fmaf(-c0i, z0.y, fmaf(c1r, z1.x, fmaf(-c1i, z1.y, re1[f]))));
+                    im1[f] = fmaf(c0r, z0.y, fmaf(c0i, z0.x, fmaf(c1r, z1.y, fmaf(c1i, z1.x, im1[f]))));
+                } else {
+                    re1[f] = fmaf(c0r, z0.x, fmaf(c1r, z1.x, re1[f]));
+                }
+            }
+        }
+    }
+
+    __device__ __forceinline__ float re(int b) const {
+        if constexpr (PAIR) return (b & 1) ? re2[b >> 1].y : re2[b >> 1].x;
+        else return re1[b];
+    }
+    __device__ __forceinline__ float im(int b) const {
+        if constexpr (PAIR) return (b & 1) ? im2[b >> 1].y : im2[b >> 1].x;
+        else return im1[b];
+    }
+};
+
 template <int FB> struct TileOcc { static constexpr int v = FB <= 4 ? 6 : FB <= 10 ? 4 : 3; };
 
-template <int FB, bool IQ, int ST, int MODE>
+template <int FB, bool IQ, int ST, int MODE, bool W256 = false>
 __global__ void __launch_bounds__(TILE_N, TileOcc<FB>::v) tile_kernel(const TileArgs A) {
     using Row = FrameRow<FB, IQ, ST>;
     constexpr int SZ = Row::SZ;
@@ -127,9 +251,8 @@ __global__ void __launch_bounds__(TILE_N, TileOcc<FB>::v) tile_kernel(const Tile
     }
     for (int q = tid; q < Q; q += TILE_N) s_tb[q] = A.tx_tb[tile * Q + q];
 
-    float acc_r[FB], acc_i[FB];
-#pragma unroll
-    for (int b = 0; b < FB; ++b) acc_r[b] = acc_i[b] = 0.f;
+    FrameAcc<FB, IQ, ST> acc;
+    acc.zero();
     long long count = 0;
 
     const int lane = tid & 31, warp = tid >> 5;
@@ -239,18 +362,9 @@ __global__ void __launch_bounds__(TILE_N, TileOcc<FB>::v) tile_kernel(const Tile
                 const unsigned char *p0 = zrow + q * qstride + (size_t)k * (FB * SZ);
                 const unsigned char *p1 = p0 + FB * SZ;
                 uint32_t w0[Row::NW], w1[Row::NW];
-                Row::load(p0, w0);
-                Row::load(p1, w1);
-#pragma unroll
-                for (int b = 0; b < FB; ++b) {
-                    const float2 z0 = Row::get(w0, b), z1 = Row::get(w1, b);
-                    if constexpr (IQ) {
-                        acc_r[b] = fmaf(c0r, z0.x, fmaf(-c0i, z0.y, fmaf(c1r, z1.x, fmaf(-c1i, z1.y, acc_r[b]))));
-                        acc_i[b] = fmaf(c0r, z0.y, fmaf(c0i, z0.x, fmaf(c1r, z1.y, fmaf(c1i, z1.x, acc_i[b]))));
-                    } else {
-                        acc_r[b] = fmaf(c0r, z0.x, fmaf(c1r, z1.x, acc_r[b]));
-                    }
-                }
+                load_row<FB, IQ, ST, W256>(p0, w0);
+                load_row<FB, IQ, ST, W256>(p1, w1);
+                acc.template add<FB>(0, w0, w1, c0r, c0i, c1r, c1i);
             }
         }
     }
@@ -261,8 +375,8 @@ __global__ void __launch_bounds__(TILE_N, TileOcc<FB>::v) tile_kernel(const Tile
             for (int b = 0; b < FB; ++b) {
                 if (b0 + b < A.B) {
                     const size_t o = (size_t)(b0 + b) * g.n_voxels + n;
-                    if constexpr (IQ) reinterpret_cast<float2 *>(A.x)[o] = make_float2(acc_r[b], acc_i[b]);
-                    else reinterpret_cast<float *>(A.x)[o] = acc_r[b];
+                    if constexpr (IQ) reinterpret_cast<float2 *>(A.x)[o] = make_float2(acc.re(b), acc.im(b));
+                    else reinterpret_cast<float *>(A.x)[o] = acc.re(b);
                 }
             }
         }
@@ -277,9 +391,9 @@ __global__ void __launch_bounds__(TILE_N, TileOcc<FB>::v) tile_kernel(const Tile
                     const size_t o = (size_t)(b0 + b) * g.n_voxels + n;
                     if constexpr (IQ) {
                         const float2 gv = reinterpret_cast<const float2 *>(A.gx)[o];
-                        v += (double)gv.x * acc_r[b] + (double)gv.y * acc_i[b];
+                        v += (double)gv.x * acc.re(b) + (double)gv.y * acc.im(b);
                     } else {
-                        v += (double)reinterpret_cast<const float *>(A.gx)[o] * acc_r[b];
+                        v += (double)reinterpret_cast<const float *>(A.gx)[o] * acc.re(b);
                     }
                 }
             }
@@ -301,10 +415,10 @@ inline size_t tile_smem_bytes(int Q, bool has_w) {
            sizeof(int) * (2 * TILE_N + Q + 5);
 }
 
-template <int FB, bool IQ, int ST, int MODE>
+template <int FB, bool IQ, int ST, int MODE, bool W256 = false>
 cudaError_t launch_tile_t(const TileArgs &A, int n_chunks, cudaStream_t s) {
     const size_t smem = tile_smem_bytes(A.Q, A.w_tx != nullptr);
-    auto kern = tile_kernel<FB, IQ, ST, MODE>;
+    auto kern = tile_kernel<FB, IQ, ST, MODE, W256>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;

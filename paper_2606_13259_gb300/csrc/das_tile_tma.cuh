@@ -168,9 +168,8 @@ __device__ __forceinline__ bool tile_tma_body(const TileArgs &A, const long long
         *s_abort = 0;
     }
 
-    float acc_r[FB], acc_i[FB];
-#pragma unroll
-    for (int b = 0; b < FB; ++b) acc_r[b] = acc_i[b] = 0.f;
+    FrameAcc<FB, IQ, ST> acc;
+    acc.zero();
 
     // Thread 0 stages item i (element j = i / Q, transmit q = i % Q) of the
     // current element block into stage (g0 + i) % S, once every warp is done
@@ -321,8 +320,9 @@ __device__ __forceinline__ bool tile_tma_body(const TileArgs &A, const long long
                 const int u = k - win.x;
                 if (u >= 0 && u + 1 < win.y) {
                     // rows u and u+1 of the staged window, FG frames at a time
-                    constexpr int FG = (FB % 4 == 0 && RB / FB * 4 % 16 == 0) ? 4 : FB;
+                    constexpr int FG = (FB % 4 == 0 && (4 * SZ) % 16 == 0) ? 4 : FB;
                     constexpr int GW = FG * SZ / 4;  // 32-bit words per group and row
+                    static_assert((FG * SZ) % 16 == 0, "frame groups must be whole 16-byte vectors");
                     const uint32_t a0 = smem_addr(stages) + (uint32_t)((st * umax + u) * RB);
 #pragma unroll
                     for (int bg = 0; bg < FB; bg += FG) {
@@ -333,33 +333,14 @@ __device__ __forceinline__ bool tile_tma_body(const TileArgs &A, const long long
                             w0[4 * v] = x0.x; w0[4 * v + 1] = x0.y; w0[4 * v + 2] = x0.z; w0[4 * v + 3] = x0.w;
                             w1[4 * v] = x1.x; w1[4 * v + 1] = x1.y; w1[4 * v + 2] = x1.z; w1[4 * v + 3] = x1.w;
                         }
-                        using RowG = FrameRow<FG, IQ, ST>;
-#pragma unroll
-                        for (int b = 0; b < FG; ++b) {
-                            const float2 z0 = RowG::get(w0, b), z1 = RowG::get(w1, b);
-                            if constexpr (IQ) {
-                                acc_r[bg + b] = fmaf(c0r, z0.x, fmaf(-c0i, z0.y, fmaf(c1r, z1.x, fmaf(-c1i, z1.y, acc_r[bg + b]))));
-                                acc_i[bg + b] = fmaf(c0r, z0.y, fmaf(c0i, z0.x, fmaf(c1r, z1.y, fmaf(c1i, z1.x, acc_i[bg + b]))));
-                            } else {
-                                acc_r[bg + b] = fmaf(c0r, z0.x, fmaf(c1r, z1.x, acc_r[bg + b]));
-                            }
-                        }
+                        acc.template add<FG>(bg, w0, w1, c0r, c0i, c1r, c1i);
                     }
                 } else {
                     uint32_t w0[Row::NW], w1[Row::NW];
                     const unsigned char *p0 = zc + q * qstride + ((size_t)mm * A.K + k) * RB;
                     Row::load(p0, w0);
                     Row::load(p0 + RB, w1);
-#pragma unroll
-                    for (int b = 0; b < FB; ++b) {
-                        const float2 z0 = Row::get(w0, b), z1 = Row::get(w1, b);
-                        if constexpr (IQ) {
-                            acc_r[b] = fmaf(c0r, z0.x, fmaf(-c0i, z0.y, fmaf(c1r, z1.x, fmaf(-c1i, z1.y, acc_r[b]))));
-                            acc_i[b] = fmaf(c0r, z0.y, fmaf(c0i, z0.x, fmaf(c1r, z1.y, fmaf(c1i, z1.x, acc_i[b]))));
-                        } else {
-                            acc_r[b] = fmaf(c0r, z0.x, fmaf(c1r, z1.x, acc_r[b]));
-                        }
-                    }
+                    acc.template add<FB>(0, w0, w1, c0r, c0i, c1r, c1i);
                 }
             }
             // this warp is done with stage st
@@ -395,8 +376,8 @@ __device__ __forceinline__ bool tile_tma_body(const TileArgs &A, const long long
             for (int b = 0; b < FB; ++b) {
                 if (b0 + b < A.B) {
                     const size_t o = (size_t)(b0 + b) * g.n_voxels + n;
-                    if constexpr (IQ) reinterpret_cast<float2 *>(A.x)[o] = make_float2(acc_r[b], acc_i[b]);
-                    else reinterpret_cast<float *>(A.x)[o] = acc_r[b];
+                    if constexpr (IQ) reinterpret_cast<float2 *>(A.x)[o] = make_float2(acc.re(b), acc.im(b));
+                    else reinterpret_cast<float *>(A.x)[o] = acc.re(b);
                 }
             }
         }
@@ -409,9 +390,9 @@ __device__ __forceinline__ bool tile_tma_body(const TileArgs &A, const long long
                     const size_t o = (size_t)(b0 + b) * g.n_voxels + n;
                     if constexpr (IQ) {
                         const float2 gv = reinterpret_cast<const float2 *>(A.gx)[o];
-                        v += (double)gv.x * acc_r[b] + (double)gv.y * acc_i[b];
+                        v += (double)gv.x * acc.re(b) + (double)gv.y * acc.im(b);
                     } else {
-                        v += (double)reinterpret_cast<const float *>(A.gx)[o] * acc_r[b];
+                        v += (double)reinterpret_cast<const float *>(A.gx)[o] * acc.re(b);
                     }
                 }
             }
@@ -457,14 +438,18 @@ cudaError_t launch_tile_tma_t(const TileArgs &A, int n_chunks, cudaStream_t s) {
 }
 
 // The staged kernel where its rows are whole 16-byte vectors, staging is on
-// (umax > 0) and the window buffers fit comfortably in shared memory; the
-// plain tile kernel otherwise.
+// (umax > 0) and the window buffers fit comfortably in shared memory; else
+// the tile kernel reading rows from global memory (256-bit loads on request
+// where rows are whole 32-byte vectors).
 template <int FB, bool IQ, int ST, int MODE>
 cudaError_t launch_tile_best(const TileArgs &A, int n_chunks, cudaStream_t s) {
     constexpr int RB = FB * SampleSize<IQ, ST>::v;
     if constexpr (RB % 16 == 0) {
         if (A.umax > 0 && tile_tma_smem_bytes(A.Q, A.w_tx != nullptr, A.umax, RB) <= 96 * 1024)
             return launch_tile_tma_t<FB, IQ, ST, MODE>(A, n_chunks, s);
+    }
+    if constexpr (MODE == MODE_FWD && IQ && RB % 32 == 0) {
+        if (A.w256) return launch_tile_t<FB, IQ, ST, MODE, true>(A, n_chunks, s);
     }
     return launch_tile_t<FB, IQ, ST, MODE>(A, n_chunks, s);
 }

@@ -122,8 +122,9 @@ class Plan:
         L.check(self._lib.das_plan_info(self._h, C.byref(i)))
         return {f: getattr(i, f) for f, _ in L.PlanInfo._fields_}
 
-    def set_tuning(self, frames_per_thread: int = 0, ctas_per_sm: int = 0, staging: bool = True) -> None:
-        t = L.Tuning(int(frames_per_thread), int(ctas_per_sm), 0 if staging else 1)
+    def set_tuning(self, frames_per_thread: int = 0, ctas_per_sm: int = 0, staging: bool = False,
+                   load_width: int = 0) -> None:
+        t = L.Tuning(int(frames_per_thread), int(ctas_per_sm), 1 if staging else 0, int(load_width))
         L.check(self._lib.das_plan_set_tuning(self._h, C.byref(t)))
 
     def check(self, stream=None) -> None:
@@ -272,7 +273,7 @@ class Batch:
             pass
 
     def set_tuning(self, frames_per_thread: int = 0, ctas_per_sm: int = 0) -> None:
-        t = L.Tuning(int(frames_per_thread), int(ctas_per_sm), 0)
+        t = L.Tuning(int(frames_per_thread), int(ctas_per_sm), 1, 0)
         L.check(self._lib.das_batch_set_tuning(self._h, C.byref(t)))
 
     def info(self) -> dict:

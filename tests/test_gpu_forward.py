@@ -172,17 +172,17 @@ def test_invalid_arguments_raise(das):
         das.Plan.from_scene(sc.with_(c=-1.0))
 
 
-@pytest.mark.parametrize("staging", [True, False])
-@pytest.mark.parametrize("fb,storage", [(2, "f32"), (8, "f32"), (20, "f32"), (4, "f16"), (12, "bf16")])
-def test_staged_and_global_sample_windows(das, oracle, staging, fb, storage):
-    """Sample windows staged in shared memory by bulk copies and rows read
-    straight from global memory give the same image; the plan records no
-    kernel-side failure."""
+@pytest.mark.parametrize("staging,load_width", [(True, 0), (False, 128), (False, 256)])
+@pytest.mark.parametrize("fb,storage", [(2, "f32"), (8, "f32"), (20, "f32"), (4, "f16"), (12, "bf16"), (16, "f16")])
+def test_staged_and_global_sample_windows(das, oracle, staging, load_width, fb, storage):
+    """Sample windows staged in shared memory by bulk copies, and rows read
+    straight from global memory with 128- or 256-bit loads, give the same
+    image; the plan records no kernel-side failure."""
     sc = ragged_scene(*RAGGED[0])
     B = 23
     y = S.random_channels(sc, B, seed=8)
     plan = das.Plan.from_scene(sc, storage=storage, max_batch=B)
-    plan.set_tuning(frames_per_thread=fb, staging=staging)
+    plan.set_tuning(frames_per_thread=fb, staging=staging, load_width=load_width)
     x = plan.forward(y.cuda()).cpu().numpy().reshape(B, -1)
     plan.check()
     plan.close()
