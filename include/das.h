@@ -72,7 +72,9 @@ enum {
 enum {
     DAS_STORE_F32 = 0,
     DAS_STORE_F16 = 1, /* half, with a float32 scale per (transmit, element) */
-    DAS_STORE_BF16 = 2 /* bfloat16, with a float32 scale per (transmit, element) */
+    DAS_STORE_BF16 = 2, /* bfloat16, with a float32 scale per (transmit, element) */
+    DAS_STORE_E4M3 = 3  /* 8-bit float E4M3 (IQ data only; the paper's future-work format), the largest
+                           component of each (transmit, element) scaled to 448 */
 };
 
 /* Receive array (Sec. 2: receivers r_m, each with an origin and a direction). */

@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(HERE, "libdas_gb300.so")
 DAS_OK, DAS_ERR_INVALID_ARG, DAS_ERR_CUDA, DAS_ERR_OOM, DAS_ERR_UNSUPPORTED, DAS_ERR_TIMEOUT = range(6)
 DAS_TX_DIVERGING, DAS_TX_PLANE, DAS_TX_NONE = 0, 1, 2
 DAS_SAMPLE_F32, DAS_SAMPLE_C64 = 0, 1
-DAS_STORE_F32, DAS_STORE_F16, DAS_STORE_BF16 = 0, 1, 2
+DAS_STORE_F32, DAS_STORE_F16, DAS_STORE_BF16, DAS_STORE_E4M3 = 0, 1, 2, 3
 
 ERROR_NAMES = {DAS_ERR_INVALID_ARG: "invalid argument", DAS_ERR_CUDA: "CUDA error", DAS_ERR_OOM: "out of memory",
                DAS_ERR_UNSUPPORTED: "unsupported", DAS_ERR_TIMEOUT: "timeout"}

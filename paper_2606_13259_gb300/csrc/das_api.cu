@@ -117,7 +117,7 @@ int sample_bytes_public(const das_plan *p) { return is_iq(p) ? 8 : 4; }
 
 int sample_bytes_store(const das_plan *p) {
     const int comp = is_iq(p) ? 2 : 1;
-    return comp * (p->storage == DAS_STORE_F32 ? 4 : 2);
+    return comp * (p->storage == DAS_STORE_F32 ? 4 : p->storage == DAS_STORE_E4M3 ? 1 : 2);
 }
 
 const int FB_F32[] = {20, 16, 12, 8, 4, 2, 1};
@@ -283,8 +283,10 @@ int das_plan_create(das_plan_t **out, const das_geometry_t *geometry, const das_
     if (options->n_samples < 2) return fail(DAS_ERR_INVALID_ARG, "n_samples must be >= 2");
     if (options->sample_type != DAS_SAMPLE_F32 && options->sample_type != DAS_SAMPLE_C64)
         return fail(DAS_ERR_INVALID_ARG, "unknown sample_type %d", options->sample_type);
-    if (options->storage < DAS_STORE_F32 || options->storage > DAS_STORE_BF16)
+    if (options->storage < DAS_STORE_F32 || options->storage > DAS_STORE_E4M3)
         return fail(DAS_ERR_INVALID_ARG, "unknown storage %d", options->storage);
+    if (options->storage == DAS_STORE_E4M3 && options->sample_type != DAS_SAMPLE_C64)
+        return fail(DAS_ERR_UNSUPPORTED, "E4M3 storage is provided for IQ data only");
     if (options->max_batch < 1) return fail(DAS_ERR_INVALID_ARG, "max_batch must be >= 1");
     if (options->sample_type == DAS_SAMPLE_F32 && f_demod != 0.0)
         return fail(DAS_ERR_INVALID_ARG, "real RF data (DAS_SAMPLE_F32) need f_demod = 0");

@@ -7,12 +7,14 @@ namespace das {
 cudaError_t launch_tile_f32(const TileArgs &A, int mode, int iq, int fb, int n_chunks, cudaStream_t s);
 cudaError_t launch_tile_f16(const TileArgs &A, int mode, int iq, int fb, int n_chunks, cudaStream_t s);
 cudaError_t launch_tile_bf16(const TileArgs &A, int mode, int iq, int fb, int n_chunks, cudaStream_t s);
+cudaError_t launch_tile_e4m3(const TileArgs &A, int mode, int iq, int fb, int n_chunks, cudaStream_t s);
 
 bool tile_fb_supported(int mode, int iq, int store, int fb) {
     (void)iq;
     if (mode == MODE_COUNT) return fb == 1;
     if (store == ST_F32) return fb == 1 || fb == 2 || fb == 4 || fb == 8 || fb == 12 || fb == 16 || fb == 20;
     if (mode != MODE_FWD) return false;
+    if (store == ST_E4M3 && !iq) return false;
     return fb == 1 || fb == 2 || fb == 4 || fb == 8 || fb == 12 || fb == 16 || fb == 20 || fb == 24;
 }
 
@@ -20,6 +22,7 @@ cudaError_t launch_tile(const TileArgs &A, int mode, int iq, int store, int fb, 
     if (!tile_fb_supported(mode, iq, store, fb)) return cudaErrorInvalidValue;
     if (mode == MODE_COUNT || store == ST_F32) return launch_tile_f32(A, mode, iq, fb, n_chunks, s);
     if (store == ST_F16) return launch_tile_f16(A, mode, iq, fb, n_chunks, s);
+    if (store == ST_E4M3) return launch_tile_e4m3(A, mode, iq, fb, n_chunks, s);
     return launch_tile_bf16(A, mode, iq, fb, n_chunks, s);
 }
 

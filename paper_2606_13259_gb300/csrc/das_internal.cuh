@@ -27,6 +27,7 @@
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -38,7 +39,7 @@ constexpr int TILE_Z = 4;
 constexpr int TILE_N = TILE_X * TILE_Y * TILE_Z;  // 128 voxels, one per thread
 constexpr float APERTURE_MARGIN = 1e-6f;
 
-enum Store { ST_F32 = 0, ST_F16 = 1, ST_BF16 = 2 };
+enum Store { ST_F32 = 0, ST_F16 = 1, ST_BF16 = 2, ST_E4M3 = 3 };
 enum Mode { MODE_FWD = 0, MODE_DC = 1, MODE_COUNT = 2 };
 
 struct GridDesc {

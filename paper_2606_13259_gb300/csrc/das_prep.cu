@@ -86,6 +86,7 @@ template <int ST> struct StoreT;
 template <> struct StoreT<ST_F32> { using c = float2; using r = float; };
 template <> struct StoreT<ST_F16> { using c = __half2; using r = __half; };
 template <> struct StoreT<ST_BF16> { using c = __nv_bfloat162; using r = __nv_bfloat16; };
+template <> struct StoreT<ST_E4M3> { using c = __nv_fp8x2_storage_t; using r = __nv_fp8_storage_t; };
 
 __device__ inline void put(float2 *p, float2 v) { *p = v; }
 __device__ inline void put(__half2 *p, float2 v) { *p = __floats2half2_rn(v.x, v.y); }
@@ -93,6 +94,10 @@ __device__ inline void put(__nv_bfloat162 *p, float2 v) { *p = __floats2bfloat16
 __device__ inline void put(float *p, float v) { *p = v; }
 __device__ inline void put(__half *p, float v) { *p = __float2half_rn(v); }
 __device__ inline void put(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+__device__ inline void put(__nv_fp8_storage_t *p, float v) { *p = __nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3); }
+__device__ inline void put(__nv_fp8x2_storage_t *p, float2 v) {
+    *p = __nv_cvt_float2_to_fp8x2(v, __NV_SATFINITE, __NV_E4M3);
+}
 
 __device__ inline float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 
@@ -100,9 +105,12 @@ __device__ inline float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x
 // scale: per (q, m) row set, the largest |component| over frames and samples
 // ---------------------------------------------------------------------------
 
+// The scale maps the largest component to `range` (1 for 16-bit storage, the
+// largest finite E4M3 value for 8-bit storage).
 template <bool IQ>
 __global__ void __launch_bounds__(256) scale_kernel(const float *__restrict__ y, float *__restrict__ scale,
-                                                    float *__restrict__ inv_scale, int B, int QM, int K) {
+                                                    float *__restrict__ inv_scale, int B, int QM, int K,
+                                                    float range) {
     const int qm = blockIdx.x;
     const int comp = IQ ? 2 : 1;
     float mx = 0.f;
@@ -118,7 +126,7 @@ __global__ void __launch_bounds__(256) scale_kernel(const float *__restrict__ y,
         mx = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         if (threadIdx.x == 0) {
-            const float s = (mx > 0.f && isfinite(mx)) ? mx : 1.f;
+            const float s = (mx > 0.f && isfinite(mx)) ? mx / range : 1.f;
             scale[qm] = s;
             inv_scale[qm] = 1.f / s;
         }
@@ -127,9 +135,9 @@ __global__ void __launch_bounds__(256) scale_kernel(const float *__restrict__ y,
 
 cudaError_t launch_scale(const void *y, float *scale, float *inv_scale, int iq, int store, int B, int QM, int K,
                          cudaStream_t s) {
-    (void)store;
-    if (iq) scale_kernel<true><<<QM, 256, 0, s>>>((const float *)y, scale, inv_scale, B, QM, K);
-    else scale_kernel<false><<<QM, 256, 0, s>>>((const float *)y, scale, inv_scale, B, QM, K);
+    const float range = store == ST_E4M3 ? 448.f : 1.f;
+    if (iq) scale_kernel<true><<<QM, 256, 0, s>>>((const float *)y, scale, inv_scale, B, QM, K, range);
+    else scale_kernel<false><<<QM, 256, 0, s>>>((const float *)y, scale, inv_scale, B, QM, K, range);
     return cudaGetLastError();
 }
 
@@ -240,7 +248,8 @@ cudaError_t launch_relayout(const void *y, void *z, const float2 *rot, const flo
     if (iq) {
         if (store == ST_F32) relayout_dispatch<true, ST_F32>(y, z, rot, inv_scale, B, fb, nch, QM, K, s);
         else if (store == ST_F16) relayout_dispatch<true, ST_F16>(y, z, rot, inv_scale, B, fb, nch, QM, K, s);
-        else relayout_dispatch<true, ST_BF16>(y, z, rot, inv_scale, B, fb, nch, QM, K, s);
+        else if (store == ST_BF16) relayout_dispatch<true, ST_BF16>(y, z, rot, inv_scale, B, fb, nch, QM, K, s);
+        else relayout_dispatch<true, ST_E4M3>(y, z, rot, inv_scale, B, fb, nch, QM, K, s);
     } else {
         if (store == ST_F32) relayout_dispatch<false, ST_F32>(y, z, rot, inv_scale, B, fb, nch, QM, K, s);
         else if (store == ST_F16) relayout_dispatch<false, ST_F16>(y, z, rot, inv_scale, B, fb, nch, QM, K, s);

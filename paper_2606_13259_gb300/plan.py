@@ -14,7 +14,7 @@ import torch
 
 from . import _lib as L
 
-STORAGE = {"f32": L.DAS_STORE_F32, "f16": L.DAS_STORE_F16, "bf16": L.DAS_STORE_BF16}
+STORAGE = {"f32": L.DAS_STORE_F32, "f16": L.DAS_STORE_F16, "bf16": L.DAS_STORE_BF16, "e4m3": L.DAS_STORE_E4M3}
 
 
 def _stream(stream: Optional[torch.cuda.Stream]) -> C.c_void_p:
