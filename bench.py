@@ -43,7 +43,7 @@ def parse_args():
                          "launch; table1: the paper's Table 1 configuration (B 128, Q 1, K 256)")
     ap.add_argument("--frames", type=int, default=20)
     ap.add_argument("--K", type=int, default=2048, help="samples per channel (all delays lie below 400)")
-    ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32")
+    ap.add_argument("--storage", choices=["f32", "f16", "bf16", "e4m3"], default="f32")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -271,7 +271,7 @@ def run_batched(args):
     # each plan alone, for reference (own launches, own tuned shape)
     alone = []
     for p, y, o in zip(plans, ys, outs):
-        autotune.tune_plan(p, y, o, staging=(True,), reps=2)
+        autotune.tune_plan(p, y, o, reps=2)
         t = autotune._time(lambda: p.forward(y, o), max(2, args.steps // 2), 1)
         alone.append(y.shape[0] / (t * 1e-3))
     actives = [p.count_active() for p in plans]
@@ -285,7 +285,7 @@ def run_batched(args):
         "vs_baseline": None, "dtype": "f16 storage, f32 arithmetic", "data": "synthetic",
         "config": {"workload": "batched_3plans_64frames",
                    "plans": [dict(sc.describe(), frames=f) for sc, f in zip(scenes, frames)],
-                   "tuning": {k: tuned[k] for k in ("frames_per_thread", "ctas_per_sm")},
+                   "tuning": {k: tuned[k] for k in ("frames_per_thread", "ctas_per_sm", "staging")},
                    "work_items": info["work_items"]},
         "per_plan_volumes_per_s_in_batch": [f / (ms * 1e-3) for f in frames],
         "per_plan_volumes_per_s_alone": alone,

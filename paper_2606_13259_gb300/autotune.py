@@ -64,15 +64,15 @@ def _time(fn, reps: int, warmup: int) -> float:
 
 
 def tune_batch(batch: Batch, ys, outs, fbs: Optional[Iterable[int]] = None,
-               ctas: Iterable[int] = (0, 1, 2, 3), reps: int = 3, warmup: int = 1,
+               ctas: Iterable[int] = (0, 1, 2, 3), staging=(False, True), reps: int = 3, warmup: int = 1,
                use_cache: bool = True) -> dict:
-    """Pick (frames per thread, CTAs per SM) for a batch; applies and returns it."""
+    """Pick (frames per thread, CTAs per SM, staged windows) for a batch; applies and returns it."""
     key = "batch:" + torch.cuda.get_device_name() + ":" + ";".join(
         f"{_plan_sig(p)}/B{f}" for p, f in zip(batch.plans, batch.frames))
     if use_cache:
         hit = _load().get(key)
         if hit:
-            batch.set_tuning(hit["frames_per_thread"], hit["ctas_per_sm"])
+            batch.set_tuning(hit["frames_per_thread"], hit["ctas_per_sm"], hit.get("staging", False))
             return dict(hit, cached=True)
     p0 = batch.plans[0]
     if fbs is None:
@@ -80,16 +80,17 @@ def tune_batch(batch: Batch, ys, outs, fbs: Optional[Iterable[int]] = None,
     results = []
     for fb in fbs:
         for c in ctas:
-            try:
-                batch.set_tuning(fb, c)
-            except L.DASError:
-                continue
-            ms = _time(lambda: batch.forward(ys, outs), reps, warmup)
-            results.append({"frames_per_thread": fb, "ctas_per_sm": c, "ms": ms})
+            for st in staging:
+                try:
+                    batch.set_tuning(fb, c, st)
+                except L.DASError:
+                    continue
+                ms = _time(lambda: batch.forward(ys, outs), reps, warmup)
+                results.append({"frames_per_thread": fb, "ctas_per_sm": c, "staging": st, "ms": ms})
     best = min(results, key=lambda r: r["ms"])
-    batch.set_tuning(best["frames_per_thread"], best["ctas_per_sm"])
-    out = {"frames_per_thread": best["frames_per_thread"], "ctas_per_sm": best["ctas_per_sm"], "ms": best["ms"],
-           "candidates": results}
+    batch.set_tuning(best["frames_per_thread"], best["ctas_per_sm"], best["staging"])
+    out = {"frames_per_thread": best["frames_per_thread"], "ctas_per_sm": best["ctas_per_sm"],
+           "staging": best["staging"], "ms": best["ms"], "candidates": results}
     if use_cache:
         _store(key, out)
     return dict(out, cached=False)

@@ -28,7 +28,7 @@ struct AdjTileRec {
 };
 
 template <bool IQ, int FB>
-__global__ void __launch_bounds__(ADJ_THREADS, 1) adjoint_kernel(const AdjArgs A) {
+__global__ void __launch_bounds__(ADJ_THREADS, 2) adjoint_kernel(const AdjArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int C = IQ ? 2 : 1;
     const int m = blockIdx.x;
@@ -49,9 +49,19 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1) adjoint_kernel(const AdjArgs A
     const float4 nn = A.elem_nrm[m];
     const long long ntiles = n_tiles(g);
 
-    const int slot = tid / TILE_N, vl = tid % TILE_N;
-    int lx, ly, lz;
-    lane_offset(vl, lx, ly, lz);
+    // Warp w, lane l: tile slot l / 8 of the ADJ_SLOTS tiles in flight, and
+    // within that tile the voxels x in {2a, 2a+1}, y = b, z = 0..3 (a, b from
+    // w).  Lanes that add into shared memory together then sit at different
+    // depths or in different tiles and mostly hit different sample rows.
+    const int slot = (tid & 31) >> 3;
+    const int wsub = tid >> 5, l8 = tid & 7;
+    const int lx = 2 * (wsub & 3) + (l8 & 1), ly = wsub >> 2, lz = l8 >> 1;
+    int vl = 0;  // tile lane of voxel (lx, ly, lz): index of the per-voxel transmit tables
+    for (int c = 0; c < TILE_N; ++c) {
+        int cx, cy, cz;
+        lane_offset(c, cx, cy, cz);
+        if (cx == lx && cy == ly && cz == lz) vl = c;
+    }
     const float dx = (float)(g.sx * (lx - 0.5 * (TILE_X - 1)));
     const float dy = (float)(g.sy * (ly - 0.5 * (TILE_Y - 1)));
     const float dz = (float)(g.sz * (lz - 0.5 * (TILE_Z - 1)));

@@ -606,7 +606,7 @@ int das_adjoint(das_plan_t *plan, const void *x_dev, void *y_dev, int batch, das
     if ((rc = prepare_if_dirty(plan, s)) != DAS_OK) return rc;
     const bool iq = is_iq(plan);
     const size_t esz = iq ? 8 : 4;
-    const size_t budget = 180 * 1024;
+    const size_t budget = 96 * 1024;  // two CTAs of 512 threads per SM
     int fb = 1, qc = 0;
     const int fbs[3] = {4, 2, 1};
     for (int i = 0; i < 3; ++i) {
@@ -955,7 +955,8 @@ extern "C" int das_batch_forward(das_batch_t *b, const void *const *y_dev, void 
             kernels += (int)(p->launches - l0);
             P.plans[i] = tile_args(p, b->frames[i], b->fb, z);
             P.plans[i].x = x_dev[i];
-            if (P.plans[i].umax <= 0) P.plans[i].umax = window_rows((p->fs / p->c) * (double)P.plans[i].tile_radius);
+            P.plans[i].w256 = 0;
+            P.plans[i].umax = b->tuning.staging ? window_rows((p->fs / p->c) * (double)P.plans[i].tile_radius) : 0;
         }
         cudaError_t e = cudaSuccess;
         if (rc == DAS_OK) {
@@ -964,7 +965,8 @@ extern "C" int das_batch_forward(das_batch_t *b, const void *const *y_dev, void 
             P.counter = b->counter;
             e = cudaMemsetAsync(b->counter, 0, sizeof(int), b->cap);
             if (e == cudaSuccess)
-                e = launch_batch(P, b->n, is_iq(b->plans[0]), b->plans[0]->storage, b->fb, b->tuning.ctas_per_sm, b->cap);
+                e = launch_batch(P, b->n, is_iq(b->plans[0]), b->plans[0]->storage, b->fb, b->tuning.ctas_per_sm,
+                                 b->tuning.staging, b->cap);
             kernels += 1;
         }
         cudaGraph_t graph = nullptr;

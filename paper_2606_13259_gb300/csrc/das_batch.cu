@@ -11,12 +11,16 @@ bool batch_fb_supported(int iq, int store, int fb) {
     return store == ST_F32 && (fb == 4 || fb == 8 || fb == 12 || fb == 16 || fb == 20);
 }
 
-#define DAS_BATCH_IQ(FB, ST) \
-    case FB: return launch_batch_t<FB, true, ST>(P, n_plans, ctas_per_sm, s);
-#define DAS_BATCH_RF(FB) \
-    case FB: return launch_batch_t<FB, false, ST_F32>(P, n_plans, ctas_per_sm, s);
+#define DAS_BATCH_IQ(FB, ST)                                                        \
+    case FB:                                                                        \
+        return staged ? launch_batch_t<FB, true, ST, true>(P, n_plans, ctas_per_sm, s) \
+                      : launch_batch_t<FB, true, ST, false>(P, n_plans, ctas_per_sm, s);
+#define DAS_BATCH_RF(FB)                                                               \
+    case FB:                                                                           \
+        return staged ? launch_batch_t<FB, false, ST_F32, true>(P, n_plans, ctas_per_sm, s) \
+                      : launch_batch_t<FB, false, ST_F32, false>(P, n_plans, ctas_per_sm, s);
 
-cudaError_t launch_batch(const BatchParams &P, int n_plans, int iq, int store, int fb, int ctas_per_sm,
+cudaError_t launch_batch(const BatchParams &P, int n_plans, int iq, int store, int fb, int ctas_per_sm, int staged,
                          cudaStream_t s) {
     if (!batch_fb_supported(iq, store, fb)) return cudaErrorInvalidValue;
     if (iq && store == ST_F32) {

@@ -23,7 +23,9 @@ struct BatchParams {
     int *counter;
 };
 
-template <int FB, bool IQ, int ST>
+// STAGED: the tile body with sample windows staged by bulk copies; else the
+// tile body reading rows from global memory.
+template <int FB, bool IQ, int ST, bool STAGED>
 __global__ void __launch_bounds__(TILE_N, TmaOcc<FB>::v) batch_kernel(const __grid_constant__ BatchParams P) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_item;
@@ -34,25 +36,30 @@ __global__ void __launch_bounds__(TILE_N, TmaOcc<FB>::v) batch_kernel(const __gr
         __syncthreads();  // all threads have the item before thread 0 takes the next one
         if (it >= P.n_items) break;
         const int4 w = P.items[it];
-        if (!tile_tma_body<FB, IQ, ST, MODE_FWD>(P.plans[w.x], w.z, w.y, smem, 0)) break;
+        if constexpr (STAGED) {
+            if (!tile_tma_body<FB, IQ, ST, MODE_FWD>(P.plans[w.x], w.z, w.y, smem, 0)) break;
+        } else {
+            tile_body<FB, IQ, ST, MODE_FWD>(P.plans[w.x], w.z, w.y, smem, 0);
+        }
     }
 }
 
 // Dynamic shared memory of the batch kernel: the largest per-plan need.
-inline size_t batch_smem_bytes(const BatchParams &P, int n_plans, int rb) {
+inline size_t batch_smem_bytes(const BatchParams &P, int n_plans, int rb, bool staged) {
     size_t m = 0;
     for (int i = 0; i < n_plans; ++i) {
-        const size_t b = tile_tma_smem_bytes(P.plans[i].Q, P.plans[i].w_tx != nullptr, P.plans[i].umax, rb);
+        const size_t b = staged ? tile_tma_smem_bytes(P.plans[i].Q, P.plans[i].w_tx != nullptr, P.plans[i].umax, rb)
+                                : tile_smem_bytes(P.plans[i].Q, P.plans[i].w_tx != nullptr);
         m = b > m ? b : m;
     }
     return m;
 }
 
-template <int FB, bool IQ, int ST>
+template <int FB, bool IQ, int ST, bool STAGED>
 cudaError_t launch_batch_t(const BatchParams &P, int n_plans, int ctas_per_sm, cudaStream_t s) {
     constexpr int RB = FB * SampleSize<IQ, ST>::v;
-    const size_t smem = batch_smem_bytes(P, n_plans, RB);
-    auto kern = batch_kernel<FB, IQ, ST>;
+    const size_t smem = batch_smem_bytes(P, n_plans, RB, STAGED);
+    auto kern = batch_kernel<FB, IQ, ST, STAGED>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, occ = 0;
@@ -68,7 +75,7 @@ cudaError_t launch_batch_t(const BatchParams &P, int n_plans, int ctas_per_sm, c
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch(const BatchParams &P, int n_plans, int iq, int store, int fb, int ctas_per_sm,
+cudaError_t launch_batch(const BatchParams &P, int n_plans, int iq, int store, int fb, int ctas_per_sm, int staged,
                          cudaStream_t s);
 bool batch_fb_supported(int iq, int store, int fb);
 

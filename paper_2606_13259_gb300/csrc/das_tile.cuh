@@ -222,13 +222,16 @@ template <int FB, bool IQ, int ST> struct FrameAcc {
     }
 };
 
-template <int FB> struct TileOcc { static constexpr int v = FB <= 4 ? 6 : FB <= 10 ? 4 : 3; };
+template <int FB> struct TileOcc { static constexpr int v = FB <= 4 ? 6 : FB <= 12 ? 5 : 4; };
 
+// One (tile, frame chunk) of one plan with rows read from global memory;
+// `smem` is the CTA's dynamic shared memory (tile_smem_bytes).  Called by
+// tile_kernel (one launch per plan) and by the persistent batch kernel.
 template <int FB, bool IQ, int ST, int MODE, bool W256 = false>
-__global__ void __launch_bounds__(TILE_N, TileOcc<FB>::v) tile_kernel(const TileArgs A) {
+__device__ __forceinline__ void tile_body(const TileArgs &A, const long long tile, const int chunk,
+                                          unsigned char *smem, const unsigned grid_x) {
     using Row = FrameRow<FB, IQ, ST>;
     constexpr int SZ = Row::SZ;
-    extern __shared__ __align__(16) unsigned char smem[];
     const int Q = A.Q;
     const bool has_w = A.w_tx != nullptr;
     float4 *s_eg = reinterpret_cast<float4 *>(smem);                  // [128] (G, |G|)
@@ -241,8 +244,7 @@ __global__ void __launch_bounds__(TILE_N, TileOcc<FB>::v) tile_kernel(const Tile
     int *s_cnt = s_tb + Q;                                              // [5]
 
     const int tid = threadIdx.x;
-    const long long tile = blockIdx.x;
-    const int b0 = blockIdx.y * FB;
+    const int b0 = chunk * FB;
     const GridDesc &g = A.g;
     const int tx = (int)(tile % g.tiles_x);
     const int ty = (int)((tile / g.tiles_x) % g.tiles_y);
@@ -259,6 +261,7 @@ __global__ void __launch_bounds__(TILE_N, TileOcc<FB>::v) tile_kernel(const Tile
     const float dz = (float)(g.sz * (lz - 0.5 * (TILE_Z - 1)));
     const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
 
+    __syncthreads();  // a previous body call on this CTA is done with shared memory
     for (int q = 0; q < Q; ++q) {
         s_t[q * TILE_N + tid] = A.tx_t[(tile * Q + q) * TILE_N + tid];
         if (has_w) s_w[q * TILE_N + tid] = A.w_tx[(tile * Q + q) * TILE_N + tid];
@@ -332,7 +335,7 @@ __global__ void __launch_bounds__(TILE_N, TileOcc<FB>::v) tile_kernel(const Tile
             const float r = Nn.w + A.a * __fdividef(num, d + G.w);
             // chunk-major rows: z[chunk][q][m][k][FB]
             const unsigned char *zrow = reinterpret_cast<const unsigned char *>(A.z) +
-                                        (((size_t)blockIdx.y * Q * A.M + mm) * A.K) * (size_t)(FB * SZ);
+                                        (((size_t)chunk * Q * A.M + mm) * A.K) * (size_t)(FB * SZ);
             const size_t qstride = (size_t)A.M * A.K * (FB * SZ);
 #pragma unroll 2
             for (int q = 0; q < Q; ++q) {
@@ -375,10 +378,16 @@ __global__ void __launch_bounds__(TILE_N, TileOcc<FB>::v) tile_kernel(const Tile
                 }
                 const unsigned char *p0 = zrow + q * qstride + (size_t)k * (FB * SZ);
                 const unsigned char *p1 = p0 + FB * SZ;
-                uint32_t w0[Row::NW], w1[Row::NW];
-                load_row<FB, IQ, ST, W256>(p0, w0);
-                load_row<FB, IQ, ST, W256>(p1, w1);
-                acc.template add<FB>(0, w0, w1, c0r, c0i, c1r, c1i);
+                // rows k and k+1 in groups of FG frames (fewer live registers)
+                constexpr int FG = (FB % 4 == 0 && (4 * SZ) % 16 == 0 && !W256) ? 4 : FB;
+                using RowG = FrameRow<FG, IQ, ST>;
+#pragma unroll
+                for (int bg = 0; bg < FB; bg += FG) {
+                    uint32_t w0[RowG::NW], w1[RowG::NW];
+                    load_row<FG, IQ, ST, W256>(p0 + bg * SZ, w0);
+                    load_row<FG, IQ, ST, W256>(p1 + bg * SZ, w1);
+                    acc.template add<FG>(bg, w0, w1, c0r, c0i, c1r, c1i);
+                }
             }
         }
     }
@@ -412,16 +421,23 @@ __global__ void __launch_bounds__(TILE_N, TileOcc<FB>::v) tile_kernel(const Tile
                 }
             }
         }
-        __shared__ double red[TILE_N / 32];
+        double *red = reinterpret_cast<double *>(s_eg);
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        __syncthreads();  // every warp is done reading the element records red reuses
         if (lane == 0) red[warp] = v;
         __syncthreads();
         if (tid == 0) {
             double s = 0.0;
             for (int w = 0; w < TILE_N / 32; ++w) s += red[w];
-            A.partial[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = s;
+            A.partial[(size_t)chunk * grid_x + tile] = s;
         }
     }
+}
+
+template <int FB, bool IQ, int ST, int MODE, bool W256 = false>
+__global__ void __launch_bounds__(TILE_N, TileOcc<FB>::v) tile_kernel(const TileArgs A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    tile_body<FB, IQ, ST, MODE, W256>(A, blockIdx.x, blockIdx.y, smem, gridDim.x);
 }
 
 inline size_t tile_smem_bytes(int Q, bool has_w) {

@@ -272,8 +272,8 @@ class Batch:
         except Exception:
             pass
 
-    def set_tuning(self, frames_per_thread: int = 0, ctas_per_sm: int = 0) -> None:
-        t = L.Tuning(int(frames_per_thread), int(ctas_per_sm), 1, 0)
+    def set_tuning(self, frames_per_thread: int = 0, ctas_per_sm: int = 0, staging: bool = False) -> None:
+        t = L.Tuning(int(frames_per_thread), int(ctas_per_sm), 1 if staging else 0, 0)
         L.check(self._lib.das_batch_set_tuning(self._h, C.byref(t)))
 
     def info(self) -> dict:
