@@ -507,7 +507,7 @@ def main():
     fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     flops = active * F * 16.0          # 8 FMA per contributing (voxel, element, transmit, frame) term
     achieved = flops / (kern_ms * 1e-3) / 1e12
-    bytes_store = {"f32": 8, "f16": 4, "bf16": 4}[args.storage]
+    bytes_store = {"f32": 8, "f16": 4, "bf16": 4, "e4m3": 2}[args.storage]
     alg_bytes = sc.Q * sc.M * sc.K * F * bytes_store + F * sc.N * 8
     roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
             "frac": achieved / fp32_peak, "traffic": profiled_traffic(args.storage),

@@ -222,7 +222,11 @@ template <int FB, bool IQ, int ST> struct FrameAcc {
     }
 };
 
-template <int FB> struct TileOcc { static constexpr int v = FB <= 4 ? 6 : FB <= 12 ? 5 : 4; };
+// Resident CTAs per SM asked of the compiler: wide rows of float32 IQ samples
+// (16 or more frames, 8 bytes each) keep 3 CTAs, which avoids spilling.
+template <int FB, int SZ = 4> struct TileOcc {
+    static constexpr int v = FB <= 4 ? 6 : FB <= 12 ? 5 : (SZ >= 8 ? 3 : 4);
+};
 
 // One (tile, frame chunk) of one plan with rows read from global memory;
 // `smem` is the CTA's dynamic shared memory (tile_smem_bytes).  Called by
@@ -435,7 +439,7 @@ __device__ __forceinline__ void tile_body(const TileArgs &A, const long long til
 }
 
 template <int FB, bool IQ, int ST, int MODE, bool W256 = false>
-__global__ void __launch_bounds__(TILE_N, TileOcc<FB>::v) tile_kernel(const TileArgs A) {
+__global__ void __launch_bounds__(TILE_N, (TileOcc<FB, SampleSize<IQ, ST>::v>::v)) tile_kernel(const TileArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     tile_body<FB, IQ, ST, MODE, W256>(A, blockIdx.x, blockIdx.y, smem, gridDim.x);
 }
