@@ -498,8 +498,18 @@ def main():
             plan.forward_host(y_host, x_host)
         dt = (time.perf_counter() - t0) / n_e2e
         (dt,) = max_over_ranks([dt], dist, dev)
+        # the copy legs alone, for the record
+        t1 = time.perf_counter()
+        y.copy_(y_host, non_blocking=True)
+        torch.cuda.synchronize()
+        h2d = time.perf_counter() - t1
+        t1 = time.perf_counter()
+        x_host.copy_(out, non_blocking=True)
+        torch.cuda.synchronize()
+        d2h = time.perf_counter() - t1
         e2e = {"value": world * F / dt, "unit": "volumes/s", "h2d_bytes_per_step": y_host.numel() * 8,
-               "d2h_bytes_per_step": x_host.numel() * 8, "ms_per_step": dt * 1e3}
+               "d2h_bytes_per_step": x_host.numel() * 8, "ms_per_step": dt * 1e3,
+               "h2d_ms_torch_copy": h2d * 1e3, "d2h_ms_torch_copy": d2h * 1e3}
         del y_host, x_host
 
     peaks, peak_src = measured_peaks()

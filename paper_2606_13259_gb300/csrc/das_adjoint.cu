@@ -27,21 +27,6 @@ struct AdjTileRec {
     int pad;
 };
 
-// acc[0] += a, acc[1] += b as one 64-bit compare-and-swap loop on shared
-// memory (acc 8-byte aligned): one atomic for both parts of a complex value.
-__device__ __forceinline__ void shared_add_complex(float *acc, float a, float b) {
-    unsigned long long *p = reinterpret_cast<unsigned long long *>(acc);
-    unsigned long long seen = *reinterpret_cast<volatile unsigned long long *>(p), want;
-    do {
-        want = seen;
-        const float2 cur = make_float2(__uint_as_float((unsigned)(want & 0xffffffffu)),
-                                       __uint_as_float((unsigned)(want >> 32)));
-        const unsigned long long next =
-            (unsigned long long)__float_as_uint(cur.x + a) | ((unsigned long long)__float_as_uint(cur.y + b) << 32);
-        seen = atomicCAS(p, want, next);
-    } while (seen != want);
-}
-
 template <bool IQ, int FB>
 __global__ void __launch_bounds__(ADJ_THREADS, 2) adjoint_kernel(const AdjArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -187,8 +172,10 @@ __global__ void __launch_bounds__(ADJ_THREADS, 2) adjoint_kernel(const AdjArgs A
                     const float c0r = w0 * uhr, c0i = -w0 * uhi, c1r = w1 * ubr, c1i = -w1 * ubi;
 #pragma unroll
                     for (int b = 0; b < FB; ++b) {
-                        shared_add_complex(a0 + 2 * b, c0r * xr[b] - c0i * xi[b], c0r * xi[b] + c0i * xr[b]);
-                        shared_add_complex(a1 + 2 * b, c1r * xr[b] - c1i * xi[b], c1r * xi[b] + c1i * xr[b]);
+                        atomicAdd(a0 + 2 * b, c0r * xr[b] - c0i * xi[b]);
+                        atomicAdd(a0 + 2 * b + 1, c0r * xi[b] + c0i * xr[b]);
+                        atomicAdd(a1 + 2 * b, c1r * xr[b] - c1i * xi[b]);
+                        atomicAdd(a1 + 2 * b + 1, c1r * xi[b] + c1i * xr[b]);
                     }
                 } else {
                     const float w0 = w * (1.f - al), w1 = w * al;
