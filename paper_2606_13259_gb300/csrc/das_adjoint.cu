@@ -49,13 +49,13 @@ __global__ void __launch_bounds__(ADJ_THREADS, 2) adjoint_kernel(const AdjArgs A
     const float4 nn = A.elem_nrm[m];
     const long long ntiles = n_tiles(g);
 
-    // Warp w, lane l: tile slot l / 8 of the ADJ_SLOTS tiles in flight, and
-    // within that tile the voxels x in {2a, 2a+1}, y = b, z = 0..3 (a, b from
-    // w).  Lanes that add into shared memory together then sit at different
-    // depths or in different tiles and mostly hit different sample rows.
-    const int slot = (tid & 31) >> 3;
-    const int wsub = tid >> 5, l8 = tid & 7;
-    const int lx = 2 * (wsub & 3) + (l8 & 1), ly = wsub >> 2, lz = l8 >> 1;
+    // Threads 128 s .. 128 s + 127 take the tile in slot s; within it warp w
+    // holds the voxels of row y = w, lane l the voxel x = l % 8, z = l / 8.  A
+    // warp then stays inside one tile (coherent aperture decisions) and its
+    // lanes at different depths add into different sample rows; only the x
+    // neighbours at one depth can meet on a row.
+    const int slot = tid / TILE_N;
+    const int lx = tid & 7, ly = (tid >> 5) & 3, lz = (tid >> 3) & 3;
     int vl = 0;  // tile lane of voxel (lx, ly, lz): index of the per-voxel transmit tables
     for (int c = 0; c < TILE_N; ++c) {
         int cx, cy, cz;
