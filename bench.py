@@ -50,6 +50,9 @@ def parse_args():
     ap.add_argument("--staging", action="store_true", help="stage sample windows in shared memory (bulk copies)")
     ap.add_argument("--load-width", type=int, default=0, choices=[0, 128, 256], help="bits per lane of each load")
     ap.add_argument("--fb", type=int, default=0, help="frames per thread (0: automatic)")
+    ap.add_argument("--tensor-cores", action="store_true",
+                    help="forward pass as the tcgen05 tile contraction (f16 / bf16 storage)")
+    ap.add_argument("--ctas", type=int, default=0, help="CTAs per SM of the tensor-core kernel (0: automatic)")
     return ap.parse_args()
 
 
@@ -59,6 +62,30 @@ def measured_peaks():
             return json.load(f), "measured"
     except OSError:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def apply_tuning(plan, args) -> None:
+    if args.tensor_cores:
+        plan.set_tuning(tensor_cores=True, ctas_per_sm=args.ctas)
+    elif args.staging or args.fb or args.load_width:
+        plan.set_tuning(frames_per_thread=args.fb, staging=args.staging, load_width=args.load_width)
+
+
+def tensor_roofline(plan, items0: int, launches: int, kern_ms: float) -> dict:
+    """Tensor-pipe roofline of the tcgen05 kernel: MMA flops issued per launch
+    (sub-items x 2 x 128 x N x 32, counted by the kernel) over its event time,
+    against the measured sustained dense bf16 (= f16) rate."""
+    peaks, src = measured_peaks()
+    info = plan.info()
+    items = (info["tc_mma_items"] - items0) / max(launches, 1)
+    n = info["tc_mma_n"]
+    flops = items * 2.0 * 128 * n * 32
+    achieved = flops / (kern_ms * 1e-3) / 1e12
+    peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1700.0)))
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "tc_kernel (tcgen05 tile contraction)", "kernel_ms": kern_ms,
+            "peak_source": f"{src} dense bf16 sustained (f16 runs at the same rate)",
+            "work_per_launch": f"{items:.0f} MMA sub-items x 128 x {n} x 32 x 2 flop"}
 
 
 def kernel_source_hash() -> str:
@@ -315,13 +342,13 @@ def run_table1(args):
     F = 128
     y = S.frames(sc, F, seed=6, n_speckle=4000, points=S.paper_points(sc), device="cuda")
     plan = Plan.from_scene(sc, storage=args.storage, max_batch=F)
-    if args.staging or args.fb or args.load_width:
-        plan.set_tuning(frames_per_thread=args.fb, staging=args.staging, load_width=args.load_width)
+    apply_tuning(plan, args)
     out = torch.empty((F,) + plan.shape, dtype=torch.complex64, device="cuda")
     active = plan.count_active()
     for _ in range(args.warmup):
         plan.forward(y, out)
     torch.cuda.synchronize()
+    items0 = plan.info()["tc_mma_items"]
     plan.enable_timing(args.steps)
     sampler = ClockSampler(0)
     sampler.start()
@@ -347,9 +374,11 @@ def run_table1(args):
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": args.storage + " storage, f32 arithmetic", "data": "synthetic",
         "config": {"workload": sc.name, "frames_per_step": F, "scene": sc.describe()},
-        "roofline": {"bound": "alu", "achieved": flops / (kern_ms * 1e-3) / 1e12, "peak": fp32_peak,
-                     "unit": "TFLOP/s", "frac": flops / (kern_ms * 1e-3) / 1e12 / fp32_peak, "traffic": None,
-                     "kernel_ms": kern_ms},
+        "roofline": tensor_roofline(plan, items0, kn, kern_ms) if args.tensor_cores else
+        {"bound": "alu", "achieved": flops / (kern_ms * 1e-3) / 1e12, "peak": fp32_peak,
+         "unit": "TFLOP/s", "frac": flops / (kern_ms * 1e-3) / 1e12 / fp32_peak, "traffic": None,
+         "kernel_ms": kern_ms},
+        "tensor_cores": bool(args.tensor_cores),
         "gpu_launches": None, "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
@@ -449,14 +478,14 @@ def main():
     sc, y = make_inputs(args.frames, rank, dev, args.K)
     F = args.frames
     plan = Plan.from_scene(sc, storage=args.storage, max_batch=F)
-    if args.staging or args.fb or args.load_width:
-        plan.set_tuning(frames_per_thread=args.fb, staging=args.staging, load_width=args.load_width)
+    apply_tuning(plan, args)
     out = torch.empty((F,) + plan.shape, dtype=torch.complex64, device=dev)
     active = plan.count_active()
 
     for _ in range(args.warmup):
         plan.forward(y, out)
     torch.cuda.synchronize()
+    items0 = plan.info()["tc_mma_items"]
     plan.enable_timing(args.steps)
     launches0 = plan.info()["kernel_launches"]
     sampler = ClockSampler(local) if rank == 0 else None
@@ -519,7 +548,12 @@ def main():
     achieved = flops / (kern_ms * 1e-3) / 1e12
     bytes_store = {"f32": 8, "f16": 4, "bf16": 4, "e4m3": 2}[args.storage]
     alg_bytes = sc.Q * sc.M * sc.K * F * bytes_store + F * sc.N * 8
-    roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+    if args.tensor_cores:
+        roof = tensor_roofline(plan, items0, kern_n, kern_ms)
+        roof.update({"useful_flops_tflops": achieved, "hbm_algorithmic_gbs": alg_bytes / (kern_ms * 1e-3) / 1e9})
+    else:
+        roof = None
+    roof = roof or {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
             "frac": achieved / fp32_peak, "traffic": profiled_traffic(args.storage),
             "kernel": "tile_kernel (forward DAS)", "kernel_ms": kern_ms,
             "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz ({peak_src} max SM clock)",
@@ -536,7 +570,7 @@ def main():
                    "transmits": sc.Q, "samples": sc.K, "storage": args.storage,
                    "l2": f"inputs {y.numel() * 8 / 1e9:.1f} GB > 129 MB L2, no flush", "per_rank_frames": F,
                    "staging": args.staging, "load_width": args.load_width or 128,
-                   "frames_per_thread": args.fb or "auto"},
+                   "frames_per_thread": args.fb or "auto", "tensor_cores": bool(args.tensor_cores)},
         "accumulations_per_s": world * F * sc.N * sc.M * sc.Q / (ms * 1e-3),
         "contributing_terms_per_volume": active,
         "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,

@@ -120,6 +120,9 @@ typedef struct {
     long long device_bytes;   /* device memory held by the plan */
     double c;                 /* current speed of sound */
     long long kernel_launches; /* kernels this plan has launched so far */
+    long long tc_mma_items;   /* tensor-core path: MMA sub-items issued so far, each an
+                                 M 128 x N tc_mma_n x K 32 contraction (synchronises the device) */
+    int tc_mma_n;             /* tensor-core path: MMA N of the last call (0: never used) */
 } das_plan_info_t;
 
 /* Kernel launch shape, set by the autotuner (das_plan_set_tuning). */
@@ -130,6 +133,11 @@ typedef struct {
                               memory with bulk asynchronous copies; 0: read rows straight from
                               global memory (default) */
     int load_width;        /* bits per lane of each global sample load: 128 (default) or 256 */
+    int tensor_cores;      /* 1: forward pass as a tensor-core contraction (Sec. 3.4 tile
+                              reformulation on tcgen05 MMAs, IQ data with DAS_STORE_F16 or
+                              DAS_STORE_BF16 only; the weights are rounded to the storage
+                              type); 0: CUDA-core kernels (default).  Enabling it reserves
+                              the operand scratch (2 x 2 bytes per sample and frame column). */
 } das_tuning_t;
 
 /* Build a plan (Sec. 2 problem statement: grid, receivers, observations, c).
@@ -224,8 +232,10 @@ int das_batch_info(const das_batch_t *batch, int *frames_per_thread, int *n_item
 void das_batch_destroy(das_batch_t *batch);
 
 /* Waits for the stream and reports kernel-side failures recorded since the
- * last check: DAS_ERR_TIMEOUT when a kernel gave up waiting for a staged copy
- * (it then left its outputs incomplete).  Clears the record. */
+ * last check: DAS_ERR_TIMEOUT when a kernel gave up a bounded wait (on a
+ * staged copy, or inside the tensor-core pipeline) or the tensor-core path
+ * met a term outside the sample window it bounded for it (it then left its
+ * outputs incomplete).  Clears the record. */
 int das_plan_check(das_plan_t *plan, das_stream_t stream);
 
 /* Kernel timing for benchmarks.  With capacity > 0 the plan records a CUDA

@@ -49,12 +49,13 @@ class Options(C.Structure):
 class PlanInfo(C.Structure):
     _fields_ = [("n_voxels", C.c_longlong), ("n_elements", C.c_int), ("n_transmits", C.c_int),
                 ("n_samples", C.c_int), ("sample_type", C.c_int), ("storage", C.c_int), ("max_batch", C.c_int),
-                ("device_bytes", C.c_longlong), ("c", C.c_double), ("kernel_launches", C.c_longlong)]
+                ("device_bytes", C.c_longlong), ("c", C.c_double), ("kernel_launches", C.c_longlong),
+                ("tc_mma_items", C.c_longlong), ("tc_mma_n", C.c_int)]
 
 
 class Tuning(C.Structure):
     _fields_ = [("frames_per_thread", C.c_int), ("ctas_per_sm", C.c_int), ("staging", C.c_int),
-                ("load_width", C.c_int)]
+                ("load_width", C.c_int), ("tensor_cores", C.c_int)]
 
 
 class DASError(RuntimeError):

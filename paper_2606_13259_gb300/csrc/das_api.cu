@@ -50,6 +50,7 @@ struct das_plan {
     int *tx_tb = nullptr;
     float *tx_t = nullptr;
     float *tx_tmin = nullptr;
+    float *tx_tmax = nullptr;
     int *err = nullptr;
     float *w_tx = nullptr;
     float2 *rot = nullptr;
@@ -62,8 +63,14 @@ struct das_plan {
     double *scalar = nullptr;
     void *stage_y = nullptr;
     void *stage_x = nullptr;
+    void *z_tc = nullptr;      // tensor-core operand layout of the channel data
+    size_t z_tc_bytes = 0;
+    float *ratio = nullptr;    // [Q][M] scale / largest scale (tensor-core path)
+    float *smax = nullptr;     // largest scale (tensor-core path)
+    unsigned long long *tc_items = nullptr;  // MMA sub-items issued (tensor-core path)
+    int tc_n = 0;              // MMA N of the last tensor-core call
     bool dirty = true;
-    das_tuning_t tuning{0, 0, 0, 0};
+    das_tuning_t tuning{0, 0, 0, 0, 0};
     size_t bytes = 0;
     long long launches = 0;
     std::vector<cudaEvent_t> ev_start, ev_stop;
@@ -176,7 +183,7 @@ int ensure_scratch(das_plan *p) {
 int prepare_if_dirty(das_plan *p, cudaStream_t s) {
     if (!p->dirty) return DAS_OK;
     DAS_CU(launch_prepare(p->g, p->Q, p->tx_kind, p->tx_vec, p->tx_off, p->t0, p->fs / p->c, p->tx_tb, p->tx_t,
-                          p->tx_tmin, s));
+                          p->tx_tmin, p->tx_tmax, s));
     p->launches += 1;
     p->dirty = false;
     return DAS_OK;
@@ -251,6 +258,95 @@ int stage_channels(das_plan *p, const void *y, int B, int fb, int nch, cudaStrea
                            p->storage, B, fb, nch, QM, p->K, s));
     p->launches += 1;
     *z_out = p->z;
+    return DAS_OK;
+}
+
+bool tc_capable(const das_plan *p) {
+    return is_iq(p) && (p->storage == DAS_STORE_F16 || p->storage == DAS_STORE_BF16);
+}
+
+// Operand scratch of the tensor-core path: chunks x (q, m) x n columns x K
+// rows x 2 planes x 2 bytes, the largest over the batch sizes the plan takes.
+size_t tc_scratch_bytes(const das_plan *p) {
+    size_t best = 0;
+    for (int B = 1; B <= p->max_batch; ++B) {
+        int bc, nch, n;
+        tc_shape(B, bc, nch, n);
+        const size_t b = (size_t)nch * p->Q * p->M * (size_t)n * p->K * 4;
+        best = b > best ? b : best;
+    }
+    return best;
+}
+
+int ensure_tc_scratch(das_plan *p) {
+    int rc;
+    if (!p->ratio && (rc = dalloc(p, (void **)&p->ratio, sizeof(float) * (size_t)p->Q * p->M, "scale ratios")) != DAS_OK)
+        return rc;
+    if (!p->smax && (rc = dalloc(p, (void **)&p->smax, sizeof(float), "largest scale")) != DAS_OK) return rc;
+    if (!p->tc_items) {
+        if ((rc = dalloc(p, (void **)&p->tc_items, sizeof(unsigned long long), "MMA item counter")) != DAS_OK) return rc;
+        DAS_CU(cudaMemset(p->tc_items, 0, sizeof(unsigned long long)));
+    }
+    const size_t need = tc_scratch_bytes(p);
+    if (need <= p->z_tc_bytes) return DAS_OK;
+    dfree(p, p->z_tc);
+    p->bytes -= p->z_tc_bytes;
+    p->z_tc = nullptr;
+    p->z_tc_bytes = 0;
+    if ((rc = dalloc(p, &p->z_tc, need, "tensor-core operand scratch")) != DAS_OK) return rc;
+    p->z_tc_bytes = need;
+    return DAS_OK;
+}
+
+// Forward pass on the tensor cores: per-(q, m) scales, the operand relayout,
+// then the tcgen05 kernel (das_tc.cu).
+int forward_tc(das_plan *p, const void *y, void *x, int B, cudaStream_t s) {
+    int bc, nch, n;
+    tc_shape(B, bc, nch, n);
+    const int QM = p->Q * p->M;
+    const size_t need = (size_t)nch * QM * (size_t)n * p->K * 4;
+    if (need > p->z_tc_bytes || !p->ratio || !p->smax)
+        return fail(DAS_ERR_INVALID_ARG, "tensor-core scratch holds %zu bytes, batch needs %zu", p->z_tc_bytes, need);
+    const bool bf16 = p->storage == DAS_STORE_BF16;
+    DAS_CU(launch_scale(y, p->scale, p->inv_scale, 1, p->storage, B, QM, p->K, s));
+    DAS_CU(launch_tc_stage(y, p->z_tc, p->rot, p->scale, p->inv_scale, p->ratio, p->smax, bf16 ? 1 : 0, B, bc, nch, n,
+                           QM, p->K, s));
+    p->launches += 3;
+    TcArgs A{};
+    A.g = p->g;
+    A.M = p->M;
+    A.Q = p->Q;
+    A.K = p->K;
+    A.B = B;
+    A.bc = bc;
+    A.n = n;
+    fill_common(p, A.a, A.ad, A.theta, A.hr, A.hi, A.thr, A.tile_radius);
+    A.ahx = (float)(A.ad * 0.5 * (TILE_X - 1) * p->g.sx);
+    A.ahy = (float)(A.ad * 0.5 * (TILE_Y - 1) * p->g.sy);
+    A.ahz = (float)(A.ad * 0.5 * (TILE_Z - 1) * p->g.sz);
+    A.aR = (float)(A.ad * A.tile_radius);
+    A.aR2h = (float)(A.ad * (double)A.tile_radius * A.tile_radius * 0.5);
+    A.elem_pos = p->elem_pos;
+    A.elem_nrm = p->elem_nrm;
+    A.tx_tb = p->tx_tb;
+    A.tx_t = p->tx_t;
+    A.tx_tmin = p->tx_tmin;
+    A.tx_tmax = p->tx_tmax;
+    A.w_tx = p->w_tx;
+    A.ratio = p->ratio;
+    A.smax = p->smax;
+    A.err = p->err;
+    A.items = p->tc_items;
+    A.x = reinterpret_cast<float2 *>(x);
+    p->tc_n = n;
+    const bool timed = p->ev_used < (int)p->ev_start.size();
+    if (timed) DAS_CU(cudaEventRecord(p->ev_start[p->ev_used], s));
+    DAS_CU(launch_tc(A, bf16 ? 1 : 0, p->z_tc, nch, p->tuning.ctas_per_sm, s));
+    p->launches += 1;
+    if (timed) {
+        DAS_CU(cudaEventRecord(p->ev_stop[p->ev_used], s));
+        p->ev_used += 1;
+    }
     return DAS_OK;
 }
 
@@ -390,6 +486,7 @@ int das_plan_create(das_plan_t **out, const das_geometry_t *geometry, const das_
     DAS_ALLOC(p->tx_tb, sizeof(int) * (size_t)T * Q, "transmit bases");
     DAS_ALLOC(p->tx_t, sizeof(float) * (size_t)T * Q * TILE_N, "transmit delays");
     DAS_ALLOC(p->tx_tmin, sizeof(float) * (size_t)T * Q, "transmit delay minima");
+    DAS_ALLOC(p->tx_tmax, sizeof(float) * (size_t)T * Q, "transmit delay maxima");
     DAS_ALLOC(p->err, sizeof(int), "device error word");
     if ((e0 = cudaMemset(p->err, 0, sizeof(int))) != cudaSuccess) return bail(cuda_fail(e0, "cudaMemset"));
     DAS_ALLOC(p->partial, sizeof(double) * (size_t)T * p->max_batch, "partials");
@@ -479,6 +576,14 @@ int das_plan_info(const das_plan_t *plan, das_plan_info_t *info) {
     info->device_bytes = (long long)plan->bytes;
     info->c = plan->c;
     info->kernel_launches = plan->launches;
+    info->tc_mma_n = plan->tc_n;
+    info->tc_mma_items = 0;
+    if (plan->tc_items) {
+        DeviceGuard guard(plan->device);
+        unsigned long long v = 0;
+        DAS_CU(cudaMemcpy(&v, plan->tc_items, sizeof(v), cudaMemcpyDeviceToHost));
+        info->tc_mma_items = (long long)v;
+    }
     return DAS_OK;
 }
 
@@ -491,7 +596,7 @@ int das_plan_check(das_plan_t *plan, das_stream_t stream) {
     if (flags) {
         DAS_CU(cudaMemsetAsync(plan->err, 0, sizeof(int), (cudaStream_t)stream));
         DAS_CU(cudaStreamSynchronize((cudaStream_t)stream));
-        return fail(DAS_ERR_TIMEOUT, "a kernel gave up waiting for a staged copy (error word 0x%x)", flags);
+        return fail(DAS_ERR_TIMEOUT, "a kernel gave up a bounded wait or lost a term (error word 0x%x)", flags);
     }
     return DAS_OK;
 }
@@ -531,8 +636,10 @@ int das_plan_timing(das_plan_t *plan, double *ms_total, int *launches) {
 
 int das_plan_set_tuning(das_plan_t *plan, const das_tuning_t *tuning) {
     if (!plan || !tuning) return fail(DAS_ERR_INVALID_ARG, "NULL argument");
-    if (tuning->frames_per_thread < 0 || tuning->ctas_per_sm < 0 || tuning->staging < 0)
+    if (tuning->frames_per_thread < 0 || tuning->ctas_per_sm < 0 || tuning->staging < 0 || tuning->tensor_cores < 0)
         return fail(DAS_ERR_INVALID_ARG, "negative tuning value");
+    if (tuning->tensor_cores && !tc_capable(plan))
+        return fail(DAS_ERR_UNSUPPORTED, "the tensor-core path takes IQ data stored as f16 or bf16");
     if (tuning->load_width != 0 && tuning->load_width != 128 && tuning->load_width != 256)
         return fail(DAS_ERR_INVALID_ARG, "load_width must be 0, 128 or 256");
     if (tuning->frames_per_thread > 0 &&
@@ -540,7 +647,9 @@ int das_plan_set_tuning(das_plan_t *plan, const das_tuning_t *tuning) {
         return fail(DAS_ERR_UNSUPPORTED, "frames_per_thread %d not compiled for this storage", tuning->frames_per_thread);
     DeviceGuard guard(plan->device);
     plan->tuning = *tuning;
-    return ensure_scratch(plan);
+    int rc = ensure_scratch(plan);
+    if (rc == DAS_OK && tuning->tensor_cores) rc = ensure_tc_scratch(plan);
+    return rc;
 }
 
 static int check_call(das_plan_t *plan, const void *a, const void *b, int batch) {
@@ -561,6 +670,7 @@ int das_forward(das_plan_t *plan, const void *y_dev, void *x_dev, int batch, das
     if (!guard.ok) return fail(DAS_ERR_CUDA, "cannot select the plan's device");
     cudaStream_t s = (cudaStream_t)stream;
     if ((rc = prepare_if_dirty(plan, s)) != DAS_OK) return rc;
+    if (plan->tuning.tensor_cores) return forward_tc(plan, y_dev, x_dev, batch, s);
     const int fb = choose_fb(plan, batch, MODE_FWD);
     const int nch = (batch + fb - 1) / fb;
     const void *z = nullptr;
@@ -911,8 +1021,9 @@ extern "C" void das_batch_destroy(das_batch_t *b) {
 
 extern "C" int das_batch_set_tuning(das_batch_t *b, const das_tuning_t *tuning) {
     if (!b || !tuning) return fail(DAS_ERR_INVALID_ARG, "NULL argument");
-    if (tuning->frames_per_thread < 0 || tuning->ctas_per_sm < 0 || tuning->staging < 0)
+    if (tuning->frames_per_thread < 0 || tuning->ctas_per_sm < 0 || tuning->staging < 0 || tuning->tensor_cores < 0)
         return fail(DAS_ERR_INVALID_ARG, "negative tuning value");
+    if (tuning->tensor_cores) return fail(DAS_ERR_UNSUPPORTED, "the batched launch runs on the CUDA cores");
     DeviceGuard guard(b->device);
     b->tuning = *tuning;
     return batch_build(b);

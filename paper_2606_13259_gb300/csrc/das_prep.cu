@@ -34,8 +34,9 @@ __global__ void __launch_bounds__(TILE_N) prepare_kernel(GridDesc g, int Q, cons
                                                          const double *__restrict__ vec,
                                                          const double *__restrict__ off, double t0x, double t0y,
                                                          double t0z, double ad, int *__restrict__ tx_tb,
-                                                         float *__restrict__ tx_t, float *__restrict__ tx_tmin) {
-    __shared__ float red[TILE_N / 32];
+                                                         float *__restrict__ tx_t, float *__restrict__ tx_tmin,
+                                                         float *__restrict__ tx_tmax) {
+    __shared__ float red[TILE_N / 32], red_max[TILE_N / 32];
     const long long tile = blockIdx.x;
     const int tx = (int)(tile % g.tiles_x);
     const int ty = (int)((tile / g.tiles_x) % g.tiles_y);
@@ -55,24 +56,35 @@ __global__ void __launch_bounds__(TILE_N) prepare_kernel(GridDesc g, int Q, cons
         const float t = (float)(ad * tx_path(kd, vx, vy, vz, o, t0x, t0y, t0z, px, py, pz) - base);
         tx_t[(tile * Q + q) * TILE_N + threadIdx.x] = t;
         if (threadIdx.x == 0) tx_tb[tile * Q + q] = (int)base;
-        float mn = valid ? t : 3.0e38f;
-        for (int d = 16; d > 0; d >>= 1) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, d));
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mn;
+        float mn = valid ? t : 3.0e38f, mx = valid ? t : -3.0e38f;
+        for (int d = 16; d > 0; d >>= 1) {
+            mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, d));
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, d));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            red[threadIdx.x >> 5] = mn;
+            red_max[threadIdx.x >> 5] = mx;
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
-            float m = red[0];
-            for (int w = 1; w < TILE_N / 32; ++w) m = fminf(m, red[w]);
+            float m = red[0], u = red_max[0];
+            for (int w = 1; w < TILE_N / 32; ++w) {
+                m = fminf(m, red[w]);
+                u = fmaxf(u, red_max[w]);
+            }
             tx_tmin[tile * Q + q] = m;
+            if (tx_tmax) tx_tmax[tile * Q + q] = u;
         }
         __syncthreads();
     }
 }
 
 cudaError_t launch_prepare(const GridDesc &g, int Q, const int *kind, const double *vec, const double *off,
-                           const double *t0, double ad, int *tx_tb, float *tx_t, float *tx_tmin, cudaStream_t s) {
+                           const double *t0, double ad, int *tx_tb, float *tx_t, float *tx_tmin, float *tx_tmax,
+                           cudaStream_t s) {
     const long long nt = n_tiles(g);
     prepare_kernel<<<(unsigned)nt, TILE_N, 0, s>>>(g, Q, kind, vec, off, t0[0], t0[1], t0[2], ad, tx_tb, tx_t,
-                                                   tx_tmin);
+                                                   tx_tmin, tx_tmax);
     return cudaGetLastError();
 }
 

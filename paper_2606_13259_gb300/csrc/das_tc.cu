@@ -1,0 +1,731 @@
+// das_tc.cu -- forward DAS of IQ data as a tensor-core contraction on
+// sm_103a: tcgen05.mma with the weights and the accumulator in tensor memory
+// (TMEM) and the sample windows brought into shared memory by TMA.
+//
+// Formulation (the tile reformulation of the paper's tensor-core kernel,
+// Sec. 3.4, Alg. 3, regrouped for the 128-row MMA of this GPU).  For a tile
+// of 128 voxels (one MMA row each), one chunk of bc frames and one
+// (element m, transmit q) item, the part of Eq. 2 contributed by the item is
+//
+//     X[v][b] += sum_u W[v][u] Z[k0 + u][b],      u = 0 .. U-1  (U = 16 rows),
+//
+// where Z are the pre-rotated samples (z[k] = y[k] e^{i theta k}) of the
+// item's window of rows k0 .. k0 + U - 1, and row v of W holds the two
+// interpolation weights of voxel v, (1 - alpha) e^{i theta alpha} at
+// u = k - k0 and alpha e^{-i theta (1 - alpha)} at u + 1, times the
+// apodisation; every other entry is zero.  In real arithmetic, with
+// W = Wr + i Wi and Z = Zr + i Zi,
+//
+//     [Xr | Xi] += [Wr | Wi] . [[Zr, Zi], [-Zi, Zr]],
+//
+// one MMA of M = 128, N = 2 bc (padded to a multiple of 16, at most 256) and
+// K = 2 U = 32 (two K = 16 steps of kind::f16), accumulated in float32 in
+// TMEM over all items of the tile.
+//
+// Window of an item.  With f = rf + t + delta (das_internal.cuh), t between
+// the tile's smallest and largest transmit rest (prepare kernel) and delta =
+// a (|G + D| - |G|) bounded below by the tangent plane, a u.D >= -a sum_i
+// |u_i| h_i, and above by min(a u.D + a R^2 / (2 |G|), a R) (G the element to
+// tile-centre vector, u = G / |G|, h the half extents of the tile, R its
+// radius), every k of the tile lies in [klo, khi] computed from per-item
+// values alone.  Each thread derives the same [klo, khi], so the producer can
+// fetch windows ahead of the threads that build W.  Items whose range spans
+// more than U - 1 = 15 values of k are split into several MMA sub-items with
+// windows 15 rows apart (none at the workloads of the paper).
+//
+// Operand layouts.
+//   A (W): TMEM, lanes = voxels (tile lane order), 16 columns of 32 bits per
+//          stage = 32 16-bit values, K-major: columns 0-7 Wr (u = 0..15),
+//          8-15 Wi.  Four stages.
+//   B (window): shared memory, MN-major without swizzle.  The relayout
+//          stores the channel data as z[c][q m][n / 8][plane][k][8] 16-bit
+//          values, plane 0 = [Zr | Zi] and plane 1 = [-Zi | Zr] along n, so
+//          one 5-D TMA box (8, 16, 2, n / 8, 1) at row k0 lands as core
+//          matrices of 8 n x 8 K values (128 B): K-direction stride 128 B,
+//          n-direction stride 512 B.  Rows outside 0 .. K-1 arrive as zeros.
+//   D: TMEM columns 0 .. n-1, lanes = voxels.
+//
+// CTA roles (192 threads): warps 0-3 build W (thread = voxel = TMEM lane) and
+// run the epilogue; warp 4 lane 0 issues the window copies; warp 5 lane 0
+// issues the MMAs and their commits.  Stages are handed over with mbarriers:
+// fullA (128 builder arrivals), fullB (TMA transaction bytes), emptyA /
+// emptyB (tcgen05.commit of the MMAs that read the stage), accFull (commit
+// after the last MMA).  Every wait is bounded; on expiry the CTA sets bit 2
+// of the plan's error word, drains what it has in flight and leaves without
+// writing its image tile.
+#include "das_async.cuh"
+#include "das_internal.cuh"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+namespace das {
+
+constexpr int TC_THREADS = 192;
+constexpr int TC_U = 16;        // window rows per sub-item
+constexpr int TC_KV = TC_U - 1; // values of k a sub-item covers
+constexpr int TC_SA = 4;        // W stages in TMEM
+constexpr int TC_ACOLS = 16;    // TMEM columns per W stage
+constexpr int TC_EB = 512;      // element records per block
+constexpr int TC_MAX_SB = 24;
+constexpr float TC_MARGIN = 0.02f;  // samples
+
+// ---------------------------------------------------------------------------
+// tcgen05 / TMA primitives (inline PTX)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(dst)),
+                 "r"(ncols)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15, %16};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]),
+        "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// D[tmem] (+)= A[tmem] . B[smem], kind::f16, one CTA.
+__device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
+                                       uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Arrive on `bar` once every MMA this thread issued so far has completed.
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3, int c4,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+        "%6}], [%7];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor, no swizzle: start address, K-direction and
+// MN-direction strides between 8 x 16-byte core matrices (bytes).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t k_stride, uint32_t mn_stride) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((k_stride >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((mn_stride >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: float32 accumulator, A and B both f16
+// (or both bf16), A K-major, B MN-major, M = 128, N = n.
+__host__ __device__ constexpr uint32_t tc_idesc(int n, bool bf16) {
+    return (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) | (1u << 16) |
+           ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+template <bool BF16>
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+    if constexpr (BF16) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+        return *reinterpret_cast<uint32_t *>(&h);
+    } else {
+        __half2 h = __floats2half2_rn(lo, hi);
+        return *reinterpret_cast<uint32_t *>(&h);
+    }
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+constexpr uint64_t TC_WAIT_NS = 1000000000ull;  // 1 s
+
+// Bounded wait (1 s of wall time); gives up early when another role of the
+// CTA, or another CTA, has recorded a timeout.
+__device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity, volatile uint32_t *abort_flag, int *err) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t i = 1;; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 63u) == 0u) {
+            if (*abort_flag || (*(volatile int *)err & 4)) {
+                *abort_flag = 1u;
+                return false;
+            }
+            if (global_ns() - t0 > TC_WAIT_NS) break;
+        }
+    }
+    atomicOr(err, 4);
+    *abort_flag = 1u;
+    return false;
+}
+
+// Sub-items of one item: the range [klo, khi] every k of the tile lies in,
+// clipped to the valid rows; returns the number of 15-value windows (0: no
+// term of the item can be valid).
+__device__ __forceinline__ int tc_item(int tb, int rb, float rf, float tmin, float tmax, float2 gb, int K, int &klo) {
+    int lo = tb + rb + (int)floorf(rf + tmin + gb.x);
+    int hi = tb + rb + (int)floorf(rf + tmax + gb.y);
+    lo = max(lo, 0);
+    hi = min(hi, K - 2);
+    klo = lo;
+    return hi < lo ? 0 : (hi - lo) / TC_KV + 1;
+}
+
+// ---------------------------------------------------------------------------
+// the kernel
+// ---------------------------------------------------------------------------
+
+struct TcSmem {
+    size_t bars, misc, eg, en, gb, erb, em, t, w, tb, tmin, tmax, total;
+};
+
+__host__ __device__ inline TcSmem tc_smem_layout(int sb, int n, int Q, bool has_w) {
+    TcSmem L{};
+    size_t o = (size_t)sb * 64 * n;  // window stages (1024-aligned base)
+    L.bars = o; o += 64 * 8;
+    L.misc = o; o += 64;
+    L.eg = o; o += (size_t)TC_EB * 16;
+    L.en = o; o += (size_t)TC_EB * 16;
+    L.gb = o; o += (size_t)TC_EB * 8;
+    L.erb = o; o += (size_t)TC_EB * 4;
+    L.em = o; o += (size_t)TC_EB * 4;
+    L.t = o; o += (size_t)Q * TILE_N * 4;
+    L.w = o; o += has_w ? (size_t)Q * TILE_N * 4 : 0;
+    L.tb = o; o += (size_t)Q * 4;
+    L.tmin = o; o += (size_t)Q * 4;
+    L.tmax = o; o += (size_t)Q * 4;
+    L.total = o + 1024;  // alignment slack of the dynamic base
+    return L;
+}
+
+template <bool BF16, int MINB>
+__global__ void __launch_bounds__(TC_THREADS, MINB) tc_kernel(const __grid_constant__ CUtensorMap zmap,
+                                                              const __grid_constant__ TcArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
+    const int Q = A.Q, M = A.M, K = A.K, n = A.n, sb = A.sb;
+    const bool has_w = A.w_tx != nullptr;
+    const TcSmem L = tc_smem_layout(sb, n, Q, has_w);
+    const uint32_t stage_bytes = 64u * (uint32_t)n;
+    unsigned char *sB = smem;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L.bars);
+    uint64_t *fullB = bars, *emptyB = bars + TC_MAX_SB, *fullA = bars + 2 * TC_MAX_SB, *emptyA = fullA + TC_SA;
+    uint64_t *accFull = emptyA + TC_SA;
+    uint32_t *misc = reinterpret_cast<uint32_t *>(smem + L.misc);  // tmem, abort, issued, total, counts[4]
+    volatile uint32_t *s_abort = misc + 1;
+    float4 *s_eg = reinterpret_cast<float4 *>(smem + L.eg);
+    float4 *s_en = reinterpret_cast<float4 *>(smem + L.en);
+    float2 *s_gb = reinterpret_cast<float2 *>(smem + L.gb);
+    int *s_erb = reinterpret_cast<int *>(smem + L.erb);
+    int *s_em = reinterpret_cast<int *>(smem + L.em);
+    float *s_t = reinterpret_cast<float *>(smem + L.t);
+    float *s_w = reinterpret_cast<float *>(smem + L.w);
+    int *s_tb = reinterpret_cast<int *>(smem + L.tb);
+    float *s_tmin = reinterpret_cast<float *>(smem + L.tmin);
+    float *s_tmax = reinterpret_cast<float *>(smem + L.tmax);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long tile = blockIdx.x;
+    const int chunk = blockIdx.y;
+    const GridDesc &g = A.g;
+    const int tx = (int)(tile % g.tiles_x);
+    const int ty = (int)((tile / g.tiles_x) % g.tiles_y);
+    const int tz = (int)(tile / ((long long)g.tiles_x * g.tiles_y));
+
+    if (tid == 0) {
+        for (int s = 0; s < sb; ++s) {
+            mbar_init(&fullB[s], 1);
+            mbar_init(&emptyB[s], 1);
+        }
+        for (int s = 0; s < TC_SA; ++s) {
+            mbar_init(&fullA[s], TILE_N);
+            mbar_init(&emptyA[s], 1);
+        }
+        mbar_init(accFull, 1);
+        misc[1] = (*(volatile int *)A.err & 4) ? 1u : 0u;  // another CTA already gave up: leave at once
+        misc[2] = 0u;
+        mbar_init_fence();
+    }
+    if (warp == 0) {
+        tmem_alloc(&misc[0], (uint32_t)A.ncols);
+        tmem_relinquish();
+    }
+    if (tid < TILE_N) {
+        for (int q = 0; q < Q; ++q) {
+            s_t[q * TILE_N + tid] = A.tx_t[(tile * Q + q) * TILE_N + tid];
+            if (has_w) s_w[q * TILE_N + tid] = A.w_tx[(tile * Q + q) * TILE_N + tid];
+        }
+    }
+    for (int q = tid; q < Q; q += TC_THREADS) {
+        s_tb[q] = A.tx_tb[tile * Q + q];
+        s_tmin[q] = A.tx_tmin[tile * Q + q];
+        s_tmax[q] = A.tx_tmax[tile * Q + q];
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = misc[0];
+
+    // voxel of a builder thread
+    int lx = 0, ly = 0, lz = 0;
+    lane_offset(tid & (TILE_N - 1), lx, ly, lz);
+    const int ix = tx * TILE_X + lx, iy = ty * TILE_Y + ly, iz = tz * TILE_Z + lz;
+    const bool valid = tid < TILE_N && ix < g.nx && iy < g.ny && iz < g.nz;
+    double p0x, p0y, p0z;
+    tile_centre(g, tx, ty, tz, p0x, p0y, p0z);
+    const float dx = (float)(g.sx * (lx - 0.5 * (TILE_X - 1)));
+    const float dy = (float)(g.sy * (ly - 0.5 * (TILE_Y - 1)));
+    const float dz = (float)(g.sz * (lz - 0.5 * (TILE_Z - 1)));
+    const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+
+    uint32_t it = 0;  // sub-items handled so far by this thread's role
+    const size_t qm_base = (size_t)chunk * Q * M;
+
+    for (int m0 = 0; m0 < M; m0 += TC_EB) {
+        const int mend = min(M, m0 + TC_EB);
+        // ---- compaction of the candidate elements of this block (builders) ----
+        if (tid == 0) misc[3] = 0u;
+        __syncthreads();
+        for (int mb = m0; mb < mend; mb += TILE_N) {
+            bool cand = false;
+            float4 eg = make_float4(0.f, 0.f, 0.f, 0.f), en = eg;
+            float2 gbv = make_float2(0.f, 0.f);
+            int rb = 0;
+            const int m = mb + tid;
+            if (tid < TILE_N && m < mend) {
+                const double rx = A.elem_pos[3 * m], ry = A.elem_pos[3 * m + 1], rz = A.elem_pos[3 * m + 2];
+                const double Gx = p0x - rx, Gy = p0y - ry, Gz = p0z - rz;
+                const double D0 = sqrt(Gx * Gx + Gy * Gy + Gz * Gz);
+                const double R0 = A.ad * D0;
+                const double Rf = floor(R0);
+                rb = (int)Rf;
+                const float4 nn = A.elem_nrm[m];
+                eg = make_float4((float)Gx, (float)Gy, (float)Gz, (float)D0);
+                en = make_float4(nn.x, nn.y, nn.z, (float)(R0 - Rf));
+                if (D0 > 1e-12) {
+                    const double ux = Gx / D0, uy = Gy / D0, uz = Gz / D0;
+                    const float lin = (float)(fabs(ux) * A.ahx + fabs(uy) * A.ahy + fabs(uz) * A.ahz);
+                    const float curv = (float)(A.aR2h / D0);
+                    gbv = make_float2(-lin - TC_MARGIN, fminf(lin + curv, A.aR) + TC_MARGIN);
+                } else {
+                    gbv = make_float2(-A.aR - TC_MARGIN, A.aR + TC_MARGIN);
+                }
+                cand = true;
+                if (A.thr >= 0.f) {
+                    const float z0 = eg.x * nn.x + eg.y * nn.y + eg.z * nn.z;
+                    const float cx = eg.y * nn.z - eg.z * nn.y, cy = eg.z * nn.x - eg.x * nn.z,
+                                cz = eg.x * nn.y - eg.y * nn.x;
+                    const float rho0 = sqrtf(cx * cx + cy * cy + cz * cz);
+                    const float zmax = z0 + A.tile_radius;
+                    const float rmin = fmaxf(rho0 - A.tile_radius, 0.f);
+                    cand = (zmax > 0.f) && (rmin * rmin <= A.thr * zmax * zmax * 1.001f);
+                }
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, cand);
+            if (tid < TILE_N && lane == 0) misc[4 + warp] = __popc(bal);
+            __syncthreads();
+            if (tid < TILE_N && cand) {
+                int off = (int)misc[3];
+                for (int w = 0; w < warp; ++w) off += (int)misc[4 + w];
+                const int idx = off + __popc(bal & ((1u << lane) - 1u));
+                s_eg[idx] = eg;
+                s_en[idx] = en;
+                s_gb[idx] = gbv;
+                s_erb[idx] = rb;
+                s_em[idx] = m;
+            }
+            __syncthreads();
+            if (tid == 0) misc[3] += misc[4] + misc[5] + misc[6] + misc[7];
+            __syncthreads();
+        }
+        const int n_el = (int)misc[3];
+
+        if (tid < TILE_N) {
+            // ---- builders: one row of W per voxel and sub-item ----
+            const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+            bool stop = *s_abort != 0u;
+            for (int j = 0; j < n_el && !stop; ++j) {
+                const float4 G = s_eg[j];
+                const float4 Nn = s_en[j];
+                const float2 gbv = s_gb[j];
+                const int Rb = s_erb[j];
+                const int mm = s_em[j];
+                const float ex = G.x + dx, ey = G.y + dy, ez = G.z + dz;
+                bool inside = valid;
+                if (A.thr >= 0.f) {
+                    const float zax = fmaf(ex, Nn.x, fmaf(ey, Nn.y, ez * Nn.z));
+                    const float cx = fmaf(ey, Nn.z, -ez * Nn.y), cy = fmaf(ez, Nn.x, -ex * Nn.z),
+                                cz = fmaf(ex, Nn.y, -ey * Nn.x);
+                    const float rho2 = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
+                    inside = inside && (zax > 0.f) && (rho2 <= A.thr * zax * zax);
+                }
+                const float d = sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
+                const float num = fmaf(2.f, fmaf(G.x, dx, fmaf(G.y, dy, G.z * dz)), dd);
+                const float r = Nn.w + A.a * __fdividef(num, d + G.w);
+                for (int q = 0; q < Q && !stop; ++q) {
+                    int klo;
+                    const int nsub = tc_item(s_tb[q], Rb, Nn.w, s_tmin[q], s_tmax[q], gbv, K, klo);
+                    if (nsub == 0) continue;
+                    const float f = r + s_t[q * TILE_N + tid];
+                    const float fl = floorf(f);
+                    const float al = f - fl;
+                    const int k = s_tb[q] + Rb + (int)fl;
+                    const bool act = inside && (unsigned)k <= (unsigned)(K - 2);
+                    if (act && (k < klo || k > klo + TC_KV * nsub - 1)) atomicOr(A.err, 8);
+                    float w = has_w ? s_w[q * TILE_N + tid] : 1.f;
+                    w *= __ldg(A.ratio + (size_t)q * M + mm);
+                    float sn, cs;
+                    __sincosf(A.theta * (al - 0.5f), &sn, &cs);
+                    const float uhr = cs * A.hr - sn * A.hi, uhi = cs * A.hi + sn * A.hr;  // e^{i th a}
+                    const float ubr = cs * A.hr + sn * A.hi, ubi = sn * A.hr - cs * A.hi;  // e^{-i th (1-a)}
+                    const float w0 = w * (1.f - al), w1 = w * al;
+                    const uint32_t pr = pack2<BF16>(w0 * uhr, w1 * ubr);  // (Wr[u], Wr[u+1])
+                    const uint32_t pi = pack2<BF16>(w0 * uhi, w1 * ubi);  // (Wi[u], Wi[u+1])
+                    for (int s = 0; s < nsub; ++s) {
+                        const int u = k - (klo + TC_KV * s);
+                        const bool in = act && u >= 0 && u < TC_KV;
+                        const int uw = in ? (u >> 1) : -8;
+                        const bool odd = (u & 1) != 0;
+                        const uint32_t Pr = odd ? (pr << 16) : pr, Qr = odd ? (pr >> 16) : 0u;
+                        const uint32_t Pi = odd ? (pi << 16) : pi, Qi = odd ? (pi >> 16) : 0u;
+                        uint32_t v[16];
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) {
+                            const bool e0 = c == uw, e1 = c == uw + 1;
+                            v[c] = e0 ? Pr : (e1 ? Qr : 0u);
+                            v[8 + c] = e0 ? Pi : (e1 ? Qi : 0u);
+                        }
+                        const uint32_t sa = it & (TC_SA - 1), use = it / TC_SA;
+                        bool ok = true;
+                        if (use > 0 && lane == 0) ok = tc_wait(&emptyA[sa], (use - 1) & 1u, s_abort, A.err);
+                        ok = __shfl_sync(0xffffffffu, ok, 0) != 0;
+                        if (!ok) {
+                            stop = true;
+                            break;
+                        }
+                        tc_fence_after();
+                        tmem_st16(tmem + lane_base + (uint32_t)(n + TC_ACOLS * sa), v);
+                        tmem_st_wait();
+                        tc_fence_before();
+                        mbar_arrive(&fullA[sa]);
+                        ++it;
+                    }
+                }
+            }
+        } else if (warp == 4) {
+            // ---- producer: window copies ----
+            if (lane == 0) {
+                bool stop = *s_abort != 0u;
+                for (int j = 0; j < n_el && !stop; ++j) {
+                    const float rf = s_en[j].w;
+                    const float2 gbv = s_gb[j];
+                    const int Rb = s_erb[j];
+                    const int mm = s_em[j];
+                    for (int q = 0; q < Q && !stop; ++q) {
+                        int klo;
+                        const int nsub = tc_item(s_tb[q], Rb, rf, s_tmin[q], s_tmax[q], gbv, K, klo);
+                        for (int s = 0; s < nsub; ++s) {
+                            const uint32_t slot = it % (uint32_t)sb, use = it / (uint32_t)sb;
+                            if (use > 0 && !tc_wait(&emptyB[slot], (use - 1) & 1u, s_abort, A.err)) {
+                                stop = true;
+                                break;
+                            }
+                            mbar_arrive_expect_tx(&fullB[slot], stage_bytes);
+                            tma_load_5d(sB + (size_t)slot * stage_bytes, &zmap, 0, klo + TC_KV * s, 0, 0,
+                                        (int)(qm_base + (size_t)q * M + mm), &fullB[slot]);
+                            ++it;
+                        }
+                    }
+                }
+            }
+        } else {
+            // ---- MMA issuer ----
+            if (lane == 0) {
+                const uint32_t idesc = tc_idesc(n, BF16);
+                bool stop = *s_abort != 0u;
+                for (int j = 0; j < n_el && !stop; ++j) {
+                    const float rf = s_en[j].w;
+                    const float2 gbv = s_gb[j];
+                    const int Rb = s_erb[j];
+                    for (int q = 0; q < Q && !stop; ++q) {
+                        int klo;
+                        const int nsub = tc_item(s_tb[q], Rb, rf, s_tmin[q], s_tmax[q], gbv, K, klo);
+                        for (int s = 0; s < nsub; ++s) {
+                            const uint32_t sa = it & (TC_SA - 1), slot = it % (uint32_t)sb;
+                            if (!tc_wait(&fullA[sa], (it / TC_SA) & 1u, s_abort, A.err) ||
+                                !tc_wait(&fullB[slot], (it / (uint32_t)sb) & 1u, s_abort, A.err)) {
+                                stop = true;
+                                break;
+                            }
+                            tc_fence_after();
+                            const uint32_t a_col = tmem + (uint32_t)(n + TC_ACOLS * sa);
+                            const uint32_t b_addr = smem_addr(sB + (size_t)slot * stage_bytes);
+                            mma_ts(tmem, a_col, smem_desc(b_addr, 128, 512), idesc, it > 0 ? 1u : 0u);
+                            mma_ts(tmem, a_col + 8, smem_desc(b_addr + 256, 128, 512), idesc, 1u);
+                            mma_commit(&emptyA[sa]);
+                            mma_commit(&emptyB[slot]);
+                            ++it;
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();  // element records of this block no longer read
+    }
+
+    if (warp == 5 && lane == 0) {
+        misc[2] = it;
+        if (it > 0) {
+            mma_commit(accFull);
+            atomicAdd(A.items, (unsigned long long)it);
+        }
+    }
+    __syncthreads();
+    const uint32_t issued = misc[2];
+
+    if (tid < TILE_N) {
+        // ---- epilogue: D (TMEM) -> image ----
+        // MMAs still in flight must land before the tensor memory is read or
+        // released, so this wait ignores aborts and is bounded by time only.
+        bool ok = true;
+        if (issued > 0 && lane == 0) {
+            const uint64_t t0 = global_ns();
+            while (!(ok = mbar_try_wait(accFull, 0u)))
+                if (global_ns() - t0 > TC_WAIT_NS) break;
+            if (!ok) atomicOr(A.err, 4);
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0) != 0 && *s_abort == 0u;
+        __syncwarp();
+        tc_fence_after();
+        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        const float sm = *A.smax;
+        const long long nvox = ((long long)iz * g.ny + iy) * g.nx + ix;
+        for (int b0 = 0; b0 < A.bc; b0 += 16) {
+            uint32_t re[16], im[16];
+            if (issued > 0) {
+                tmem_ld16(tmem + lane_base + (uint32_t)b0, re);
+                tmem_ld16(tmem + lane_base + (uint32_t)(A.bc + b0), im);
+                tmem_ld_wait();
+            } else {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) re[i] = im[i] = 0u;
+            }
+            if (ok && valid) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int b = b0 + i;
+                    const long long frame = (long long)chunk * A.bc + b;
+                    if (b < A.bc && frame < A.B)
+                        A.x[frame * g.n_voxels + nvox] =
+                            make_float2(__uint_as_float(re[i]) * sm, __uint_as_float(im[i]) * sm);
+                }
+            }
+        }
+        tc_fence_before();
+    } else if (warp == 4 && lane == 0 && *s_abort != 0u) {
+        // copies still in flight land before the CTA leaves
+        const uint32_t last = it;
+        const uint32_t first = last > (uint32_t)sb ? last - (uint32_t)sb : 0u;
+        const uint64_t t0 = global_ns();
+        for (uint32_t i = first; i < last; ++i) {
+            while (!mbar_try_wait(&fullB[i % (uint32_t)sb], (i / (uint32_t)sb) & 1u))
+                if (global_ns() - t0 > TC_WAIT_NS) break;
+        }
+    }
+    __syncthreads();
+    if (warp == 0) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc(tmem, (uint32_t)A.ncols);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// staging: scale ratios and the operand layout of the channel data
+// ---------------------------------------------------------------------------
+
+// ratio[qm] = scale[qm] / max(scale); *smax = max(scale).  One block.
+__global__ void __launch_bounds__(1024) tc_ratio_kernel(const float *__restrict__ scale, float *__restrict__ ratio,
+                                                        float *__restrict__ smax, int QM) {
+    __shared__ float red[32];
+    float mx = 0.f;
+    for (int i = threadIdx.x; i < QM; i += blockDim.x) mx = fmaxf(mx, scale[i]);
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    mx = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmaxf(mx, red[w]);
+    for (int i = threadIdx.x; i < QM; i += blockDim.x) ratio[i] = scale[i] / mx;
+    if (threadIdx.x == 0) *smax = mx;
+}
+
+// One thread per sample row k of one (chunk, q m): builds the n values of both
+// planes, eight at a time, each written as one 16-byte vector.
+template <bool BF16>
+__global__ void __launch_bounds__(128) tc_relayout_kernel(const float2 *__restrict__ y, uint4 *__restrict__ z,
+                                                          const float2 *__restrict__ rot,
+                                                          const float *__restrict__ inv_scale, int B, int bc, int n,
+                                                          int QM, int K) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.z;
+    if (k >= K) return;
+    const float2 r = rot ? rot[k] : make_float2(1.f, 0.f);
+    const int nh = n >> 3;
+    for (int qm = blockIdx.y; qm < QM; qm += gridDim.y) {
+        const float s = inv_scale[qm];
+        for (int h = 0; h < nh; ++h) {
+            uint32_t p[4], q[4];
+#pragma unroll
+            for (int i = 0; i < 8; i += 2) {
+                float pv[2], qv[2];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int col = 8 * h + i + e;
+                    const int f = col < bc ? col : col - bc;
+                    const long long b = (long long)c * bc + f;
+                    float2 v = make_float2(0.f, 0.f);
+                    if (col < 2 * bc && f < bc && b < B) {
+                        const float2 yv = y[((size_t)b * QM + qm) * (size_t)K + k];
+                        v = make_float2((yv.x * r.x - yv.y * r.y) * s, (yv.x * r.y + yv.y * r.x) * s);
+                    }
+                    // plane 0: [Zr | Zi], plane 1: [-Zi | Zr]
+                    pv[e] = col < bc ? v.x : v.y;
+                    qv[e] = col < bc ? -v.y : v.x;
+                }
+                p[i >> 1] = pack2<BF16>(pv[0], pv[1]);
+                q[i >> 1] = pack2<BF16>(qv[0], qv[1]);
+            }
+            const size_t row = (((size_t)c * QM + qm) * nh + h) * 2;
+            z[row * K + k] = make_uint4(p[0], p[1], p[2], p[3]);
+            z[(row + 1) * K + k] = make_uint4(q[0], q[1], q[2], q[3]);
+        }
+    }
+}
+
+void tc_shape(int B, int &bc, int &nch, int &n) {
+    nch = (B + 127) / 128;
+    bc = (B + nch - 1) / nch;
+    n = ((2 * bc + 15) / 16) * 16;
+}
+
+cudaError_t launch_tc_stage(const void *y, void *z, const float2 *rot, const float *scale, const float *inv_scale,
+                            float *ratio, float *smax, int bf16, int B, int bc, int nch, int n, int QM, int K,
+                            cudaStream_t s) {
+    tc_ratio_kernel<<<1, 1024, 0, s>>>(scale, ratio, smax, QM);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    dim3 grid((K + 127) / 128, QM < 65535 ? QM : 65535, nch);
+    if (bf16)
+        tc_relayout_kernel<true><<<grid, 128, 0, s>>>((const float2 *)y, (uint4 *)z, rot, inv_scale, B, bc, n, QM, K);
+    else
+        tc_relayout_kernel<false><<<grid, 128, 0, s>>>((const float2 *)y, (uint4 *)z, rot, inv_scale, B, bc, n, QM, K);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// launch
+// ---------------------------------------------------------------------------
+
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+template <bool BF16, int MINB>
+static cudaError_t launch_tc_t(const CUtensorMap &map, const TcArgs &A, size_t smem, int nch, cudaStream_t s) {
+    auto kern = tc_kernel<BF16, MINB>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)n_tiles(A.g), (unsigned)nch);
+    kern<<<grid, TC_THREADS, smem, s>>>(map, A);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc(const TcArgs &args, int bf16, const void *z, int nch, int ctas_per_sm, cudaStream_t s) {
+    TcArgs A = args;
+    if (A.n < 16 || A.n > 256 || A.n % 16 != 0 || A.bc < 1 || 2 * A.bc > A.n) return cudaErrorInvalidValue;
+    if (((uintptr_t)z & 15u) != 0) return cudaErrorInvalidValue;
+    PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+    if (!encode) return cudaErrorNotSupported;
+    // TMEM columns: accumulator + W stages, a power of two >= 32
+    int cols = 32;
+    while (cols < A.n + TC_SA * TC_ACOLS) cols <<= 1;
+    A.ncols = cols;
+    int per_sm = ctas_per_sm > 0 ? ctas_per_sm : 2;
+    if (per_sm > 512 / cols) per_sm = 512 / cols;
+    if (per_sm < 1) per_sm = 1;
+    const bool has_w = A.w_tx != nullptr;
+    const size_t budget = (size_t)(227 * 1024) / per_sm - 1024;  // per-CTA share incl. the runtime's reserve
+    const size_t fixed = tc_smem_layout(0, A.n, A.Q, has_w).total;
+    const size_t stage = (size_t)64 * A.n;
+    int sbv = fixed < budget ? (int)((budget - fixed) / stage) : 0;
+    if (sbv > TC_MAX_SB) sbv = TC_MAX_SB;
+    if (sbv < 2) return cudaErrorInvalidConfiguration;
+    A.sb = sbv;
+    const size_t smem = tc_smem_layout(sbv, A.n, A.Q, has_w).total;
+
+    CUtensorMap map;
+    const int QM = A.Q * A.M;
+    const cuuint64_t dims[5] = {8, (cuuint64_t)A.K, 2, (cuuint64_t)(A.n / 8), (cuuint64_t)nch * QM};
+    const cuuint64_t strides[4] = {16, (cuuint64_t)A.K * 16, (cuuint64_t)A.K * 32, (cuuint64_t)(A.n / 8) * A.K * 32};
+    const cuuint32_t box[5] = {8, (cuuint32_t)TC_U, 2, (cuuint32_t)(A.n / 8), 1};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    const CUresult r = encode(&map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 5,
+                              const_cast<void *>(z), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    if (per_sm >= 2) {
+        return bf16 ? launch_tc_t<true, 2>(map, A, smem, nch, s) : launch_tc_t<false, 2>(map, A, smem, nch, s);
+    }
+    return bf16 ? launch_tc_t<true, 1>(map, A, smem, nch, s) : launch_tc_t<false, 1>(map, A, smem, nch, s);
+}
+
+}  // namespace das

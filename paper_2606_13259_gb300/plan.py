@@ -123,8 +123,11 @@ class Plan:
         return {f: getattr(i, f) for f, _ in L.PlanInfo._fields_}
 
     def set_tuning(self, frames_per_thread: int = 0, ctas_per_sm: int = 0, staging: bool = False,
-                   load_width: int = 0) -> None:
-        t = L.Tuning(int(frames_per_thread), int(ctas_per_sm), 1 if staging else 0, int(load_width))
+                   load_width: int = 0, tensor_cores: bool = False) -> None:
+        """Kernel shape of the forward pass; tensor_cores selects the tcgen05
+        contraction (IQ data with f16 / bf16 storage)."""
+        t = L.Tuning(int(frames_per_thread), int(ctas_per_sm), 1 if staging else 0, int(load_width),
+                     1 if tensor_cores else 0)
         L.check(self._lib.das_plan_set_tuning(self._h, C.byref(t)))
 
     def check(self, stream=None) -> None:
@@ -273,7 +276,7 @@ class Batch:
             pass
 
     def set_tuning(self, frames_per_thread: int = 0, ctas_per_sm: int = 0, staging: bool = False) -> None:
-        t = L.Tuning(int(frames_per_thread), int(ctas_per_sm), 1 if staging else 0, 0)
+        t = L.Tuning(int(frames_per_thread), int(ctas_per_sm), 1 if staging else 0, 0, 0)
         L.check(self._lib.das_batch_set_tuning(self._h, C.byref(t)))
 
     def info(self) -> dict:

@@ -1,0 +1,136 @@
+"""GPU parity of the tensor-core forward path (tcgen05 tile contraction, Sec. 3.4)
+against the FP64 oracle, through the C-ABI.
+
+The path stores samples and interpolation weights as 16-bit values and sums
+in float32 (tensor memory), so it is held to the 16-bit bars: relative L2
+error <= 2e-3 with f16 storage, <= 2e-2 with bf16.  Every case also checks
+that no kernel-side failure was recorded (bounded waits, and terms falling
+outside the window the kernel bounded for them).
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2606_13259_gb300 import synth as S
+
+from test_gpu_forward import RAGGED, ragged_scene, rel_l2
+
+pytestmark = pytest.mark.gpu
+TOL = {"f16": 2e-3, "bf16": 2e-2}
+
+
+@pytest.fixture(scope="module")
+def das():
+    import __graft_entry__ as G
+
+    G.build()
+    import paper_2606_13259_gb300 as P
+
+    torch.cuda.set_device(0)
+    return P
+
+
+def tc_forward(das, scene, y, storage="f16", ctas_per_sm=0):
+    plan = das.Plan.from_scene(scene, storage=storage, max_batch=y.shape[0])
+    plan.set_tuning(tensor_cores=True, ctas_per_sm=ctas_per_sm)
+    x = plan.forward(y if y.is_cuda else y.cuda())
+    plan.check()
+    plan.close()
+    return x.reshape(y.shape[0], -1)
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_small_iq_scene(das, oracle, storage):
+    """32^3 voxels, 256 elements, IQ: windows span up to four 15-row sub-items."""
+    sc = S.scene_small_iq()
+    y = S.frames(sc, 3, seed=1, n_speckle=2000, points=S.SMALL_POINTS, noise_db=30.0)
+    x = tc_forward(das, sc, y, storage).cpu().numpy()
+    err = rel_l2(x, oracle.forward(sc, y.numpy()))
+    print(f"tensor cores {storage}: relative L2 {err:.3e}")
+    assert err <= TOL[storage]
+
+
+@pytest.mark.parametrize("case", [0, 2, 3])
+@pytest.mark.parametrize("B", [1, 5, 21])
+def test_ragged_tiles_and_transmit_kinds(das, oracle, case, B):
+    """Partial tiles, diverging / plane / no transmit, short K (terms out of range)."""
+    sc = ragged_scene(*RAGGED[case])
+    y = S.random_channels(sc, B, seed=20 + case)
+    x = tc_forward(das, sc, y).cpu().numpy()
+    assert rel_l2(x, oracle.forward(sc, y.numpy())) <= TOL["f16"]
+
+
+@pytest.mark.parametrize("B", [16, 128, 130])
+def test_mma_widths_and_frame_chunks(das, oracle, B):
+    """N = 32 and the largest N = 256 (128 frames), and two frame chunks (130 frames)."""
+    sc = ragged_scene(*RAGGED[0])
+    y = S.random_channels(sc, B, seed=B)
+    x = tc_forward(das, sc, y).cpu().numpy()
+    assert rel_l2(x, oracle.forward(sc, y.numpy())) <= TOL["f16"]
+
+
+def test_transmit_weights_and_one_cta_per_sm(das, oracle):
+    sc = ragged_scene(*RAGGED[0])
+    rng = np.random.default_rng(2)
+    sc = sc.with_(w_tx=rng.random((sc.Q, sc.N)).astype(np.float32))
+    y = S.random_channels(sc, 4, seed=3)
+    x = tc_forward(das, sc, y, ctas_per_sm=1).cpu().numpy()
+    assert rel_l2(x, oracle.forward(sc, y.numpy())) <= TOL["f16"]
+
+
+def test_without_demodulation(das, oracle):
+    sc = ragged_scene(*RAGGED[2]).with_(f_demod=0.0, t0_offset=False, K=128)
+    y = S.random_channels(sc, 2, seed=4)
+    x = tc_forward(das, sc, y).cpu().numpy()
+    assert rel_l2(x, oracle.forward(sc, y.numpy())) <= TOL["f16"]
+
+
+def test_matches_cuda_core_path(das):
+    """Same plan, same data: the tensor-core image against the float32 CUDA-core image."""
+    sc = S.scene_small_iq()
+    y = S.frames(sc, 4, seed=5, n_speckle=2000, points=S.SMALL_POINTS, device="cuda")
+    ref_plan = das.Plan.from_scene(sc, max_batch=4)
+    ref = ref_plan.forward(y).reshape(4, -1)
+    ref_plan.close()
+    x = tc_forward(das, sc, y)
+    err = float(torch.linalg.norm(x - ref) / torch.linalg.norm(ref))
+    assert err <= TOL["f16"]
+
+
+def test_paper_scale_sampled(das, oracle):
+    """128^3 voxels x 1024 elements x 16 transmits, 20 IQ frames (the benchmark's
+    workload and launch), 96 sampled voxels plus the ten point targets."""
+    sc = S.scene_paper()
+    B = 20
+    y = S.frames(sc, B, seed=2, n_speckle=20000, points=S.paper_points(sc), device="cuda")
+    x = tc_forward(das, sc, y)
+    rng = np.random.default_rng(0)
+    vox = np.concatenate([np.sort(rng.choice(sc.N, 96, replace=False)),
+                          [sc.voxel_index(*p) for p in S.paper_points(sc)]])
+    got = x[:, torch.as_tensor(vox, device="cuda")].cpu().numpy()
+    err = rel_l2(got, oracle.forward(sc, y.cpu().numpy(), voxels=vox))
+    print(f"paper scale, tensor cores: relative L2 {err:.3e}")
+    assert err <= TOL["f16"]
+
+
+def test_table1_configuration_sampled(das, oracle):
+    """The Table 1 configuration (128^3 voxels at lambda/2, 1024 elements at
+    lambda pitch, one plane wave, K = 256) with 128 frames: N = 256."""
+    sc = S.scene_table1()
+    B = 128
+    y = S.frames(sc, B, seed=4, n_speckle=20000, points=S.paper_points(sc), device="cuda")
+    x = tc_forward(das, sc, y)
+    rng = np.random.default_rng(1)
+    vox = np.concatenate([np.sort(rng.choice(sc.N, 48, replace=False)),
+                          [sc.voxel_index(*p) for p in S.paper_points(sc)]])
+    got = x[:, torch.as_tensor(vox, device="cuda")].cpu().numpy()
+    err = rel_l2(got, oracle.forward(sc, y.cpu().numpy(), voxels=vox))
+    print(f"Table 1 configuration, tensor cores: relative L2 {err:.3e}")
+    assert err <= TOL["f16"]
+
+
+def test_tensor_cores_need_16bit_iq(das):
+    with pytest.raises(das.DASError):
+        das.Plan.from_scene(S.scene_tiny(), storage="f32").set_tuning(tensor_cores=True)
+    with pytest.raises(das.DASError):
+        das.Plan.from_scene(S.scene_tiny(iq=False), storage="f16").set_tuning(tensor_cores=True)
