@@ -234,8 +234,8 @@ void das_batch_destroy(das_batch_t *batch);
 /* Waits for the stream and reports kernel-side failures recorded since the
  * last check: DAS_ERR_TIMEOUT when a kernel gave up a bounded wait (on a
  * staged copy, or inside the tensor-core pipeline) or the tensor-core path
- * met a term outside the sample window it bounded for it (it then left its
- * outputs incomplete).  Clears the record. */
+ * met an item needing more sample windows than one work list holds (it
+ * then left its outputs incomplete).  Clears the record. */
 int das_plan_check(das_plan_t *plan, das_stream_t stream);
 
 /* Kernel timing for benchmarks.  With capacity > 0 the plan records a CUDA

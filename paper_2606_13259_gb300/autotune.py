@@ -96,15 +96,23 @@ def tune_batch(batch: Batch, ys, outs, fbs: Optional[Iterable[int]] = None,
     return dict(out, cached=False)
 
 
+def _apply(plan: Plan, cfg: dict) -> None:
+    plan.set_tuning(cfg.get("frames_per_thread", 0), cfg.get("ctas_per_sm", 0), cfg.get("staging", False),
+                    cfg.get("load_width", 0), cfg.get("tensor_cores", False))
+
+
 def tune_plan(plan: Plan, y, out, fbs: Optional[Iterable[int]] = None, staging=(False, True),
-              load_widths=(128, 256), reps: int = 3, warmup: int = 1, use_cache: bool = True) -> dict:
-    """Pick (frames per thread, staged windows, load width) for single-plan forward calls."""
+              load_widths=(128, 256), tensor_cores=(False, True), reps: int = 3, warmup: int = 1,
+              use_cache: bool = True) -> dict:
+    """Pick the forward kernel of single-plan calls: CUDA-core tile kernel
+    (frames per thread, staged windows, load width) or the tensor-core tile
+    contraction (CTAs per SM), the latter for IQ plans with 16-bit storage."""
     B = y.shape[0]
     key = "plan:" + torch.cuda.get_device_name() + ":" + _plan_sig(plan) + f"/B{B}"
     if use_cache:
         hit = _load().get(key)
         if hit:
-            plan.set_tuning(hit["frames_per_thread"], 0, hit["staging"], hit.get("load_width", 0))
+            _apply(plan, hit)
             return dict(hit, cached=True)
     if fbs is None:
         fbs = [f for f in ((1,) + (F32_FB if plan.storage == "f32" else F16_FB)) if f <= max(B, 1) * 2]
@@ -112,16 +120,25 @@ def tune_plan(plan: Plan, y, out, fbs: Optional[Iterable[int]] = None, staging=(
     for fb in fbs:
         for st in staging:
             for lw in (load_widths if not st else (128,)):
+                cfg = {"tensor_cores": False, "frames_per_thread": fb, "staging": st, "load_width": lw,
+                       "ctas_per_sm": 0}
                 try:
-                    plan.set_tuning(fb, 0, st, lw)
+                    _apply(plan, cfg)
                 except L.DASError:
                     continue
-                ms = _time(lambda: plan.forward(y, out), reps, warmup)
-                results.append({"frames_per_thread": fb, "staging": st, "load_width": lw, "ms": ms})
+                results.append(dict(cfg, ms=_time(lambda: plan.forward(y, out), reps, warmup)))
+    if True in tuple(tensor_cores) and plan.iq and plan.storage in ("f16", "bf16"):
+        for ctas in (1, 2):
+            cfg = {"tensor_cores": True, "frames_per_thread": 0, "staging": False, "load_width": 0,
+                   "ctas_per_sm": ctas}
+            try:
+                _apply(plan, cfg)
+            except L.DASError:
+                continue
+            results.append(dict(cfg, ms=_time(lambda: plan.forward(y, out), reps, warmup)))
     best = min(results, key=lambda r: r["ms"])
-    plan.set_tuning(best["frames_per_thread"], 0, best["staging"], best["load_width"])
-    res = {"frames_per_thread": best["frames_per_thread"], "staging": best["staging"],
-           "load_width": best["load_width"], "ms": best["ms"], "candidates": results}
+    _apply(plan, best)
+    res = dict(best, candidates=results)
     if use_cache:
         _store(key, res)
     return dict(res, cached=False)

@@ -133,6 +133,7 @@ struct TcArgs {
     int bc;           // frames per chunk: MMA columns 0..bc-1 carry real parts, bc..2bc-1 imaginary parts
     int n;            // MMA N: 2 bc rounded up to a multiple of 16 (<= 256)
     int sb;           // window stages in shared memory
+    int sa;           // weight stages in tensor memory (power of two)
     int ncols;        // tensor-memory columns the CTA allocates
     float a;          // fs / c
     double ad;
@@ -149,7 +150,7 @@ struct TcArgs {
     const float *w_tx;
     const float *ratio;   // [Q][M] storage scale divided by the largest one
     const float *smax;    // the largest storage scale
-    int *err;             // bit 2: a wait timed out; bit 3: a term fell outside its window
+    int *err;             // bit 2: a wait timed out; bit 3: an item needed more windows than a list holds
     unsigned long long *items;  // running count of MMA sub-items (128 x n x 32 each)
     float2 *x;            // image [B][N]
 };

@@ -40,9 +40,10 @@
 //   B (window): shared memory, MN-major without swizzle.  The relayout
 //          stores the channel data as z[c][q m][n / 8][plane][k][8] 16-bit
 //          values, plane 0 = [Zr | Zi] and plane 1 = [-Zi | Zr] along n, so
-//          one 5-D TMA box (8, 16, 2, n / 8, 1) at row k0 lands as core
-//          matrices of 8 n x 8 K values (128 B): K-direction stride 128 B,
-//          n-direction stride 512 B.  Rows outside 0 .. K-1 arrive as zeros.
+//          one 4-D TMA box (16 rows x 8 values, 2, n / 8, 1) at element
+//          8 k0 lands as core matrices of 8 n x 8 K values (128 B):
+//          K-direction stride 128 B, n-direction stride 512 B.  Rows outside
+//          0 .. K-1 arrive as zeros.
 //   D: TMEM columns 0 .. n-1, lanes = voxels.
 //
 // CTA roles (192 threads): warps 0-3 build W (thread = voxel = TMEM lane) and
@@ -63,12 +64,15 @@
 
 namespace das {
 
-constexpr int TC_THREADS = 192;
+// A CTA has G groups of four builder warps (G = 2 with two CTAs per SM, 4 with
+// one), one producer warp and one MMA warp.
+__host__ __device__ constexpr int tc_threads(int G) { return G * TILE_N + 64; }
 constexpr int TC_U = 16;        // window rows per sub-item
 constexpr int TC_KV = TC_U - 1; // values of k a sub-item covers
-constexpr int TC_SA = 4;        // W stages in TMEM
+constexpr int TC_MAX_SA = 16;   // W stages in TMEM (power of two, set per launch)
 constexpr int TC_ACOLS = 16;    // TMEM columns per W stage
-constexpr int TC_EB = 512;      // element records per block
+constexpr int TC_EB = 256;           // element records per block
+constexpr int TC_LIST = 4096;        // sub-items per list round
 constexpr int TC_MAX_SB = 24;
 constexpr float TC_MARGIN = 0.02f;  // samples
 
@@ -133,12 +137,12 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
                  : "memory");
 }
 
-__device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3, int c4,
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
                                             uint64_t *bar) {
     asm volatile(
-        "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
-        "%6}], [%7];" ::"r"(smem_addr(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_addr(bar))
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar))
         : "memory");
 }
 
@@ -195,6 +199,35 @@ __device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity, volatile
     return false;
 }
 
+// mbarrier arrive by the threads whose predicate is set (no branch).
+__device__ __forceinline__ void mbar_arrive_if(uint64_t *bar, bool p) {
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %1, 0;\n\t"
+        "@q mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];\n\t}" ::"r"(smem_addr(bar)),
+        "r"((uint32_t)p)
+        : "memory");
+}
+
+// Slow path of a whole warp's wait (the first try failed): every lane takes
+// the same decisions, so the warp stays converged.
+__device__ __noinline__ bool tc_wait_warp(uint64_t *bar, uint32_t parity, volatile uint32_t *abort_flag, int *err) {
+    const uint64_t t0 = global_ns();
+    for (uint32_t i = 1;; ++i) {
+        if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
+        if ((i & 63u) == 0u) {
+            const bool give_up = __any_sync(0xffffffffu, *abort_flag != 0u || (*(volatile int *)err & 4) != 0 ||
+                                                             global_ns() - t0 > TC_WAIT_NS);
+            if (give_up) break;
+        }
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (!(*(volatile int *)err & 4) && !*abort_flag) atomicOr(err, 4);
+        *abort_flag = 1u;
+    }
+    __syncwarp();
+    return false;
+}
+
 // Sub-items of one item: the range [klo, khi] every k of the tile lies in,
 // clipped to the valid rows; returns the number of 15-value windows (0: no
 // term of the item can be valid).
@@ -212,14 +245,16 @@ __device__ __forceinline__ int tc_item(int tb, int rb, float rf, float tmin, flo
 // ---------------------------------------------------------------------------
 
 struct TcSmem {
-    size_t bars, misc, eg, en, gb, erb, em, t, w, tb, tmin, tmax, total;
+    size_t bars, misc, list, lw, eg, en, gb, erb, em, t, w, tb, tmin, tmax, total;
 };
 
 __host__ __device__ inline TcSmem tc_smem_layout(int sb, int n, int Q, bool has_w) {
     TcSmem L{};
     size_t o = (size_t)sb * 64 * n;  // window stages (1024-aligned base)
-    L.bars = o; o += 64 * 8;
-    L.misc = o; o += 64;
+    L.bars = o; o += 128 * 8;
+    L.misc = o; o += 32 * 4;
+    L.list = o; o += (size_t)TC_LIST * 8;
+    L.lw = o; o += (size_t)TC_LIST * 4;
     L.eg = o; o += (size_t)TC_EB * 16;
     L.en = o; o += (size_t)TC_EB * 16;
     L.gb = o; o += (size_t)TC_EB * 8;
@@ -234,21 +269,29 @@ __host__ __device__ inline TcSmem tc_smem_layout(int sb, int n, int Q, bool has_
     return L;
 }
 
-template <bool BF16, int MINB>
-__global__ void __launch_bounds__(TC_THREADS, MINB) tc_kernel(const __grid_constant__ CUtensorMap zmap,
-                                                              const __grid_constant__ TcArgs A) {
+// misc words of the kernel's shared memory
+enum : int { MW_TMEM = 0, MW_ABORT = 1, MW_ISSUED = 2, MW_NEL = 3, MW_NLIST = 4, MW_NEXT = 5, MW_CNT = 8,
+             MW_SCAN = 16 };
+
+template <bool BF16, int G, int MINB>
+__global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_constant__ CUtensorMap zmap,
+                                                                 const __grid_constant__ TcArgs A) {
+    constexpr int NB = G * TILE_N;  // builder threads
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
     const int Q = A.Q, M = A.M, K = A.K, n = A.n, sb = A.sb;
+    const uint32_t sa_n = (uint32_t)A.sa, sa_shift = (uint32_t)(31 - __clz(A.sa));
     const bool has_w = A.w_tx != nullptr;
     const TcSmem L = tc_smem_layout(sb, n, Q, has_w);
     const uint32_t stage_bytes = 64u * (uint32_t)n;
     unsigned char *sB = smem;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L.bars);
-    uint64_t *fullB = bars, *emptyB = bars + TC_MAX_SB, *fullA = bars + 2 * TC_MAX_SB, *emptyA = fullA + TC_SA;
-    uint64_t *accFull = emptyA + TC_SA;
-    uint32_t *misc = reinterpret_cast<uint32_t *>(smem + L.misc);  // tmem, abort, issued, total, counts[4]
-    volatile uint32_t *s_abort = misc + 1;
+    uint64_t *fullB = bars, *emptyB = bars + TC_MAX_SB, *fullA = bars + 2 * TC_MAX_SB, *emptyA = fullA + TC_MAX_SA;
+    uint64_t *accFull = emptyA + TC_MAX_SA;
+    uint32_t *misc = reinterpret_cast<uint32_t *>(smem + L.misc);
+    volatile uint32_t *s_abort = misc + MW_ABORT;
+    int2 *s_list = reinterpret_cast<int2 *>(smem + L.list);  // (window row, j | q << 9)
+    float *s_lw = reinterpret_cast<float *>(smem + L.lw);     // storage scale ratio of the item
     float4 *s_eg = reinterpret_cast<float4 *>(smem + L.eg);
     float4 *s_en = reinterpret_cast<float4 *>(smem + L.en);
     float2 *s_gb = reinterpret_cast<float2 *>(smem + L.gb);
@@ -261,6 +304,7 @@ __global__ void __launch_bounds__(TC_THREADS, MINB) tc_kernel(const __grid_const
     float *s_tmax = reinterpret_cast<float *>(smem + L.tmax);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int vl = tid & (TILE_N - 1);  // voxel lane = TMEM lane of a builder thread
     const long long tile = blockIdx.x;
     const int chunk = blockIdx.y;
     const GridDesc &g = A.g;
@@ -273,17 +317,17 @@ __global__ void __launch_bounds__(TC_THREADS, MINB) tc_kernel(const __grid_const
             mbar_init(&fullB[s], 1);
             mbar_init(&emptyB[s], 1);
         }
-        for (int s = 0; s < TC_SA; ++s) {
-            mbar_init(&fullA[s], TILE_N);
+        for (int s = 0; s < A.sa; ++s) {
+            mbar_init(&fullA[s], TILE_N / 32);  // one arrival per builder warp of the item's group
             mbar_init(&emptyA[s], 1);
         }
         mbar_init(accFull, 1);
-        misc[1] = (*(volatile int *)A.err & 4) ? 1u : 0u;  // another CTA already gave up: leave at once
-        misc[2] = 0u;
+        misc[MW_ABORT] = (*(volatile int *)A.err & 4) ? 1u : 0u;  // another CTA gave up: leave at once
+        misc[MW_ISSUED] = 0u;
         mbar_init_fence();
     }
     if (warp == 0) {
-        tmem_alloc(&misc[0], (uint32_t)A.ncols);
+        tmem_alloc(&misc[MW_TMEM], (uint32_t)A.ncols);
         tmem_relinquish();
     }
     if (tid < TILE_N) {
@@ -292,7 +336,7 @@ __global__ void __launch_bounds__(TC_THREADS, MINB) tc_kernel(const __grid_const
             if (has_w) s_w[q * TILE_N + tid] = A.w_tx[(tile * Q + q) * TILE_N + tid];
         }
     }
-    for (int q = tid; q < Q; q += TC_THREADS) {
+    for (int q = tid; q < Q; q += tc_threads(G)) {
         s_tb[q] = A.tx_tb[tile * Q + q];
         s_tmin[q] = A.tx_tmin[tile * Q + q];
         s_tmax[q] = A.tx_tmax[tile * Q + q];
@@ -300,13 +344,13 @@ __global__ void __launch_bounds__(TC_THREADS, MINB) tc_kernel(const __grid_const
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = misc[0];
+    const uint32_t tmem = misc[MW_TMEM];
 
-    // voxel of a builder thread
+    // voxel of a builder thread (both groups cover the same 128 voxels)
     int lx = 0, ly = 0, lz = 0;
-    lane_offset(tid & (TILE_N - 1), lx, ly, lz);
+    lane_offset(vl, lx, ly, lz);
     const int ix = tx * TILE_X + lx, iy = ty * TILE_Y + ly, iz = tz * TILE_Z + lz;
-    const bool valid = tid < TILE_N && ix < g.nx && iy < g.ny && iz < g.nz;
+    const bool valid = tid < NB && ix < g.nx && iy < g.ny && iz < g.nz;
     double p0x, p0y, p0z;
     tile_centre(g, tx, ty, tz, p0x, p0y, p0z);
     const float dx = (float)(g.sx * (lx - 0.5 * (TILE_X - 1)));
@@ -314,21 +358,21 @@ __global__ void __launch_bounds__(TC_THREADS, MINB) tc_kernel(const __grid_const
     const float dz = (float)(g.sz * (lz - 0.5 * (TILE_Z - 1)));
     const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
 
-    uint32_t it = 0;  // sub-items handled so far by this thread's role
+    uint32_t base = 0;  // sub-items of earlier rounds (same value in every thread)
     const size_t qm_base = (size_t)chunk * Q * M;
+    bool stop = misc[MW_ABORT] != 0u;
+    uint32_t tma_issued = 0;  // producer: window copies issued
 
     for (int m0 = 0; m0 < M; m0 += TC_EB) {
         const int mend = min(M, m0 + TC_EB);
-        // ---- compaction of the candidate elements of this block (builders) ----
-        if (tid == 0) misc[3] = 0u;
-        __syncthreads();
-        for (int mb = m0; mb < mend; mb += TILE_N) {
+        // ---- compaction of the candidate elements of this block (builder threads) ----
+        {
             bool cand = false;
             float4 eg = make_float4(0.f, 0.f, 0.f, 0.f), en = eg;
             float2 gbv = make_float2(0.f, 0.f);
             int rb = 0;
-            const int m = mb + tid;
-            if (tid < TILE_N && m < mend) {
+            const int m = m0 + tid;
+            if (tid < TC_EB && m < mend) {
                 const double rx = A.elem_pos[3 * m], ry = A.elem_pos[3 * m + 1], rz = A.elem_pos[3 * m + 2];
                 const double Gx = p0x - rx, Gy = p0y - ry, Gz = p0z - rz;
                 const double D0 = sqrt(Gx * Gx + Gy * Gy + Gz * Gz);
@@ -358,11 +402,11 @@ __global__ void __launch_bounds__(TC_THREADS, MINB) tc_kernel(const __grid_const
                 }
             }
             const unsigned bal = __ballot_sync(0xffffffffu, cand);
-            if (tid < TILE_N && lane == 0) misc[4 + warp] = __popc(bal);
+            if (tid < TC_EB && lane == 0) misc[MW_CNT + warp] = __popc(bal);
             __syncthreads();
-            if (tid < TILE_N && cand) {
-                int off = (int)misc[3];
-                for (int w = 0; w < warp; ++w) off += (int)misc[4 + w];
+            if (tid < TC_EB && cand) {
+                int off = 0;
+                for (int w = 0; w < warp; ++w) off += (int)misc[MW_CNT + w];
                 const int idx = off + __popc(bal & ((1u << lane) - 1u));
                 s_eg[idx] = eg;
                 s_en[idx] = en;
@@ -370,46 +414,113 @@ __global__ void __launch_bounds__(TC_THREADS, MINB) tc_kernel(const __grid_const
                 s_erb[idx] = rb;
                 s_em[idx] = m;
             }
-            __syncthreads();
-            if (tid == 0) misc[3] += misc[4] + misc[5] + misc[6] + misc[7];
+            if (tid == 0) {
+                int tot = 0;
+                for (int w = 0; w < TC_EB / 32; ++w) tot += (int)misc[MW_CNT + w];
+                misc[MW_NEL] = (uint32_t)tot;
+            }
             __syncthreads();
         }
-        const int n_el = (int)misc[3];
+        const int n_el = (int)misc[MW_NEL];
+        const int P = n_el * Q;  // (element, transmit) pairs, element-major
 
-        if (tid < TILE_N) {
-            // ---- builders: one row of W per voxel and sub-item ----
-            const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-            bool stop = *s_abort != 0u;
-            for (int j = 0; j < n_el && !stop; ++j) {
-                const float4 G = s_eg[j];
-                const float4 Nn = s_en[j];
-                const float2 gbv = s_gb[j];
-                const int Rb = s_erb[j];
-                const int mm = s_em[j];
-                const float ex = G.x + dx, ey = G.y + dy, ez = G.z + dz;
-                bool inside = valid;
-                if (A.thr >= 0.f) {
-                    const float zax = fmaf(ex, Nn.x, fmaf(ey, Nn.y, ez * Nn.z));
-                    const float cx = fmaf(ey, Nn.z, -ez * Nn.y), cy = fmaf(ez, Nn.x, -ex * Nn.z),
-                                cz = fmaf(ex, Nn.y, -ey * Nn.x);
-                    const float rho2 = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
-                    inside = inside && (zax > 0.f) && (rho2 <= A.thr * zax * zax);
-                }
-                const float d = sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
-                const float num = fmaf(2.f, fmaf(G.x, dx, fmaf(G.y, dy, G.z * dz)), dd);
-                const float r = Nn.w + A.a * __fdividef(num, d + G.w);
-                for (int q = 0; q < Q && !stop; ++q) {
+        for (int p0 = 0; p0 < P;) {
+            // ---- sub-item list of pairs p0 .. (as many as fit), by the builder threads ----
+            const int per = (P - p0 + NB - 1) / NB;
+            const int pa = min(P, p0 + tid * per), pe = min(P, pa + per);
+            int cnt = 0;
+            if (tid < NB) {
+                for (int p = pa; p < pe; ++p) {
+                    const int j = p / Q, q = p - j * Q;
                     int klo;
-                    const int nsub = tc_item(s_tb[q], Rb, Nn.w, s_tmin[q], s_tmax[q], gbv, K, klo);
-                    if (nsub == 0) continue;
-                    const float f = r + s_t[q * TILE_N + tid];
+                    cnt += tc_item(s_tb[q], s_erb[j], s_en[j].w, s_tmin[q], s_tmax[q], s_gb[j], K, klo);
+                }
+            }
+            // exclusive scan of cnt over the builder threads
+            int incl = cnt;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            if (tid < NB && lane == 31) misc[MW_SCAN + warp] = (uint32_t)incl;
+            if (tid == 0) {
+                misc[MW_NEXT] = (uint32_t)P;
+                misc[MW_NLIST] = 0u;
+            }
+            __syncthreads();
+            int off = incl - cnt;
+            for (int w = 0; w < warp && w < NB / 32; ++w) off += (int)misc[MW_SCAN + w];
+            if (tid < NB) {
+                for (int p = pa; p < pe; ++p) {
+                    const int j = p / Q, q = p - j * Q;
+                    int klo;
+                    int ns = tc_item(s_tb[q], s_erb[j], s_en[j].w, s_tmin[q], s_tmax[q], s_gb[j], K, klo);
+                    if (off + ns > TC_LIST) {
+                        if (ns > TC_LIST) {  // one pair wider than the whole list: keep what fits, flag it
+                            if (off == 0) {
+                                atomicOr(A.err, 8);
+                                ns = TC_LIST;
+                            }
+                        }
+                        if (off + ns > TC_LIST) {
+                            atomicMin(&misc[MW_NEXT], (uint32_t)p);
+                            break;
+                        }
+                    }
+                    const float ratio = ns > 0 ? __ldg(A.ratio + (size_t)q * M + s_em[j]) : 0.f;
+                    for (int s = 0; s < ns; ++s) {
+                        s_list[off + s] = make_int2(klo + TC_KV * s, j | (q << 9));
+                        s_lw[off + s] = ratio;
+                    }
+                    off += ns;
+                    atomicMax(&misc[MW_NLIST], (uint32_t)off);
+                }
+            }
+            __syncthreads();
+            const int n_list = (int)misc[MW_NLIST];
+            const int p_next = (int)misc[MW_NEXT];
+
+            if (tid < NB) {
+                // ---- builders: group `grp` writes the W rows of the sub-items with index = grp mod G ----
+                const uint32_t grp = (uint32_t)(tid >> 7);
+                const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+                int last_j = -1;
+                bool inside = false;
+                float r = 0.f;
+                int Rb = 0;
+                bool pending = false;  // a stored stage whose completion is not yet signalled
+                uint32_t pend_sa = 0;
+                for (int e = (int)((grp + (uint32_t)G - base % (uint32_t)G) % (uint32_t)G); e < n_list && !stop;
+                     e += G) {
+                    const uint32_t gi = base + (uint32_t)e;  // global sub-item index
+                    const int2 ent = s_list[e];
+                    const int j = ent.y & 511, q = (ent.y >> 9) & 127;
+                    if (j != last_j) {
+                        last_j = j;
+                        const float4 G4 = s_eg[j];
+                        const float4 Nn = s_en[j];
+                        Rb = s_erb[j];
+                        const float ex = G4.x + dx, ey = G4.y + dy, ez = G4.z + dz;
+                        inside = valid;
+                        if (A.thr >= 0.f) {
+                            const float zax = fmaf(ex, Nn.x, fmaf(ey, Nn.y, ez * Nn.z));
+                            const float cx = fmaf(ey, Nn.z, -ez * Nn.y), cy = fmaf(ez, Nn.x, -ex * Nn.z),
+                                        cz = fmaf(ex, Nn.y, -ey * Nn.x);
+                            const float rho2 = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
+                            inside = inside && (zax > 0.f) && (rho2 <= A.thr * zax * zax);
+                        }
+                        const float d = sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
+                        const float num = fmaf(2.f, fmaf(G4.x, dx, fmaf(G4.y, dy, G4.z * dz)), dd);
+                        r = Nn.w + A.a * __fdividef(num, d + G4.w);
+                    }
+                    const float f = r + s_t[q * TILE_N + vl];
                     const float fl = floorf(f);
                     const float al = f - fl;
                     const int k = s_tb[q] + Rb + (int)fl;
                     const bool act = inside && (unsigned)k <= (unsigned)(K - 2);
-                    if (act && (k < klo || k > klo + TC_KV * nsub - 1)) atomicOr(A.err, 8);
-                    float w = has_w ? s_w[q * TILE_N + tid] : 1.f;
-                    w *= __ldg(A.ratio + (size_t)q * M + mm);
+                    const int u = k - ent.x;
+                    float w = has_w ? s_w[q * TILE_N + vl] : 1.f;
+                    w *= s_lw[e];
                     float sn, cs;
                     __sincosf(A.theta * (al - 0.5f), &sn, &cs);
                     const float uhr = cs * A.hr - sn * A.hi, uhi = cs * A.hi + sn * A.hr;  // e^{i th a}
@@ -417,110 +528,97 @@ __global__ void __launch_bounds__(TC_THREADS, MINB) tc_kernel(const __grid_const
                     const float w0 = w * (1.f - al), w1 = w * al;
                     const uint32_t pr = pack2<BF16>(w0 * uhr, w1 * ubr);  // (Wr[u], Wr[u+1])
                     const uint32_t pi = pack2<BF16>(w0 * uhi, w1 * ubi);  // (Wi[u], Wi[u+1])
-                    for (int s = 0; s < nsub; ++s) {
-                        const int u = k - (klo + TC_KV * s);
-                        const bool in = act && u >= 0 && u < TC_KV;
-                        const int uw = in ? (u >> 1) : -8;
-                        const bool odd = (u & 1) != 0;
-                        const uint32_t Pr = odd ? (pr << 16) : pr, Qr = odd ? (pr >> 16) : 0u;
-                        const uint32_t Pi = odd ? (pi << 16) : pi, Qi = odd ? (pi >> 16) : 0u;
-                        uint32_t v[16];
+                    const bool in = act && (unsigned)u < (unsigned)TC_KV;
+                    const int uw = in ? (u >> 1) : -8;
+                    const bool odd = (u & 1) != 0;
+                    const uint32_t Pr = odd ? (pr << 16) : pr, Qr = odd ? (pr >> 16) : 0u;
+                    const uint32_t Pi = odd ? (pi << 16) : pi, Qi = odd ? (pi >> 16) : 0u;
+                    uint32_t v[16];
+                    bool prev = false;  // word c - 1 holds the first value
 #pragma unroll
-                        for (int c = 0; c < 8; ++c) {
-                            const bool e0 = c == uw, e1 = c == uw + 1;
-                            v[c] = e0 ? Pr : (e1 ? Qr : 0u);
-                            v[8 + c] = e0 ? Pi : (e1 ? Qi : 0u);
+                    for (int c = 0; c < 8; ++c) {
+                        const bool e0 = c == uw;
+                        v[c] = e0 ? Pr : (prev ? Qr : 0u);
+                        v[8 + c] = e0 ? Pi : (prev ? Qi : 0u);
+                        prev = e0;
+                    }
+                    // the group's previous store has drained while v was built: signal it
+                    tmem_st_wait();
+                    tc_fence_before();
+                    __syncwarp();
+                    mbar_arrive_if(&fullA[pend_sa], pending && lane == 0);
+                    const uint32_t sa = gi & (sa_n - 1u), use = gi >> sa_shift;
+                    const bool ready = __all_sync(0xffffffffu, use == 0 || mbar_try_wait(&emptyA[sa], (use - 1) & 1u));
+                    if (!ready && !tc_wait_warp(&emptyA[sa], (use - 1) & 1u, s_abort, A.err)) {
+                        pending = false;
+                        stop = true;
+                        break;
+                    }
+                    tc_fence_after();
+                    tmem_st16(tmem + lane_base + (uint32_t)n + TC_ACOLS * sa, v);
+                    pending = true;
+                    pend_sa = sa;
+                }
+                tmem_st_wait();
+                tc_fence_before();
+                __syncwarp();
+                mbar_arrive_if(&fullA[pend_sa], pending && lane == 0);
+            } else if (warp == NB / 32) {
+                // ---- producer: window copies ----
+                if (lane == 0) {
+                    for (int e = 0; e < n_list && !stop; ++e) {
+                        const uint32_t gi = base + (uint32_t)e;
+                        const int2 ent = s_list[e];
+                        const int j = ent.y & 511, q = (ent.y >> 9) & 127;
+                        const uint32_t slot = gi % (uint32_t)sb, use = gi / (uint32_t)sb;
+                        if (use > 0 && !tc_wait(&emptyB[slot], (use - 1) & 1u, s_abort, A.err)) {
+                            stop = true;
+                            break;
                         }
-                        const uint32_t sa = it & (TC_SA - 1), use = it / TC_SA;
-                        bool ok = true;
-                        if (use > 0 && lane == 0) ok = tc_wait(&emptyA[sa], (use - 1) & 1u, s_abort, A.err);
-                        ok = __shfl_sync(0xffffffffu, ok, 0) != 0;
-                        if (!ok) {
+                        mbar_arrive_expect_tx(&fullB[slot], stage_bytes);
+                        tma_load_4d(sB + (size_t)slot * stage_bytes, &zmap, 8 * ent.x, 0, 0,
+                                    (int)(qm_base + (size_t)q * M + s_em[j]), &fullB[slot]);
+                        tma_issued = gi + 1u;
+                    }
+                }
+            } else {
+                // ---- MMA issuer ----
+                if (lane == 0) {
+                    const uint32_t idesc = tc_idesc(n, BF16);
+                    for (int e = 0; e < n_list && !stop; ++e) {
+                        const uint32_t gi = base + (uint32_t)e;
+                        const uint32_t sa = gi & (sa_n - 1u), slot = gi % (uint32_t)sb;
+                        if (!tc_wait(&fullA[sa], (gi >> sa_shift) & 1u, s_abort, A.err) ||
+                            !tc_wait(&fullB[slot], (gi / (uint32_t)sb) & 1u, s_abort, A.err)) {
                             stop = true;
                             break;
                         }
                         tc_fence_after();
-                        tmem_st16(tmem + lane_base + (uint32_t)(n + TC_ACOLS * sa), v);
-                        tmem_st_wait();
-                        tc_fence_before();
-                        mbar_arrive(&fullA[sa]);
-                        ++it;
+                        const uint32_t a_col = tmem + (uint32_t)n + TC_ACOLS * sa;
+                        const uint32_t b_addr = smem_addr(sB + (size_t)slot * stage_bytes);
+                        mma_ts(tmem, a_col, smem_desc(b_addr, 128, 512), idesc, gi > 0 ? 1u : 0u);
+                        mma_ts(tmem, a_col + 8, smem_desc(b_addr + 256, 128, 512), idesc, 1u);
+                        mma_commit(&emptyA[sa]);
+                        mma_commit(&emptyB[slot]);
+                        misc[MW_ISSUED] = gi + 1u;
                     }
                 }
             }
-        } else if (warp == 4) {
-            // ---- producer: window copies ----
-            if (lane == 0) {
-                bool stop = *s_abort != 0u;
-                for (int j = 0; j < n_el && !stop; ++j) {
-                    const float rf = s_en[j].w;
-                    const float2 gbv = s_gb[j];
-                    const int Rb = s_erb[j];
-                    const int mm = s_em[j];
-                    for (int q = 0; q < Q && !stop; ++q) {
-                        int klo;
-                        const int nsub = tc_item(s_tb[q], Rb, rf, s_tmin[q], s_tmax[q], gbv, K, klo);
-                        for (int s = 0; s < nsub; ++s) {
-                            const uint32_t slot = it % (uint32_t)sb, use = it / (uint32_t)sb;
-                            if (use > 0 && !tc_wait(&emptyB[slot], (use - 1) & 1u, s_abort, A.err)) {
-                                stop = true;
-                                break;
-                            }
-                            mbar_arrive_expect_tx(&fullB[slot], stage_bytes);
-                            tma_load_5d(sB + (size_t)slot * stage_bytes, &zmap, 0, klo + TC_KV * s, 0, 0,
-                                        (int)(qm_base + (size_t)q * M + mm), &fullB[slot]);
-                            ++it;
-                        }
-                    }
-                }
-            }
-        } else {
-            // ---- MMA issuer ----
-            if (lane == 0) {
-                const uint32_t idesc = tc_idesc(n, BF16);
-                bool stop = *s_abort != 0u;
-                for (int j = 0; j < n_el && !stop; ++j) {
-                    const float rf = s_en[j].w;
-                    const float2 gbv = s_gb[j];
-                    const int Rb = s_erb[j];
-                    for (int q = 0; q < Q && !stop; ++q) {
-                        int klo;
-                        const int nsub = tc_item(s_tb[q], Rb, rf, s_tmin[q], s_tmax[q], gbv, K, klo);
-                        for (int s = 0; s < nsub; ++s) {
-                            const uint32_t sa = it & (TC_SA - 1), slot = it % (uint32_t)sb;
-                            if (!tc_wait(&fullA[sa], (it / TC_SA) & 1u, s_abort, A.err) ||
-                                !tc_wait(&fullB[slot], (it / (uint32_t)sb) & 1u, s_abort, A.err)) {
-                                stop = true;
-                                break;
-                            }
-                            tc_fence_after();
-                            const uint32_t a_col = tmem + (uint32_t)(n + TC_ACOLS * sa);
-                            const uint32_t b_addr = smem_addr(sB + (size_t)slot * stage_bytes);
-                            mma_ts(tmem, a_col, smem_desc(b_addr, 128, 512), idesc, it > 0 ? 1u : 0u);
-                            mma_ts(tmem, a_col + 8, smem_desc(b_addr + 256, 128, 512), idesc, 1u);
-                            mma_commit(&emptyA[sa]);
-                            mma_commit(&emptyB[slot]);
-                            ++it;
-                        }
-                    }
-                }
-            }
-        }
-        __syncthreads();  // element records of this block no longer read
-    }
-
-    if (warp == 5 && lane == 0) {
-        misc[2] = it;
-        if (it > 0) {
-            mma_commit(accFull);
-            atomicAdd(A.items, (unsigned long long)it);
+            base += (uint32_t)n_list;
+            p0 = p_next;
+            __syncthreads();  // list and element records of this round no longer read
+            stop = stop || *s_abort != 0u;
         }
     }
-    __syncthreads();
-    const uint32_t issued = misc[2];
 
-    if (tid < TILE_N) {
-        // ---- epilogue: D (TMEM) -> image ----
+    const uint32_t issued = misc[MW_ISSUED];  // written by the MMA thread before the last barrier
+    if (warp == NB / 32 + 1 && lane == 0 && issued > 0) {
+        mma_commit(accFull);
+        atomicAdd(A.items, (unsigned long long)issued);
+    }
+
+    if (tid < NB) {
+        // ---- epilogue: D (TMEM) -> image; the groups take alternate 16-frame blocks ----
         // MMAs still in flight must land before the tensor memory is read or
         // released, so this wait ignores aborts and is bounded by time only.
         bool ok = true;
@@ -533,10 +631,10 @@ __global__ void __launch_bounds__(TC_THREADS, MINB) tc_kernel(const __grid_const
         ok = __shfl_sync(0xffffffffu, ok, 0) != 0 && *s_abort == 0u;
         __syncwarp();
         tc_fence_after();
-        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
         const float sm = *A.smax;
         const long long nvox = ((long long)iz * g.ny + iy) * g.nx + ix;
-        for (int b0 = 0; b0 < A.bc; b0 += 16) {
+        for (int b0 = 16 * (tid >> 7); b0 < A.bc; b0 += 16 * G) {
             uint32_t re[16], im[16];
             if (issued > 0) {
                 tmem_ld16(tmem + lane_base + (uint32_t)b0, re);
@@ -558,9 +656,10 @@ __global__ void __launch_bounds__(TC_THREADS, MINB) tc_kernel(const __grid_const
             }
         }
         tc_fence_before();
-    } else if (warp == 4 && lane == 0 && *s_abort != 0u) {
-        // copies still in flight land before the CTA leaves
-        const uint32_t last = it;
+    } else if (warp == NB / 32 && lane == 0 && *s_abort != 0u) {
+        // copies still in flight land before the CTA leaves: wait for the
+        // last use of every stage (bounded by time)
+        const uint32_t last = tma_issued;
         const uint32_t first = last > (uint32_t)sb ? last - (uint32_t)sb : 0u;
         const uint64_t t0 = global_ns();
         for (uint32_t i = first; i < last; ++i) {
@@ -678,13 +777,13 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
-template <bool BF16, int MINB>
+template <bool BF16, int G, int MINB>
 static cudaError_t launch_tc_t(const CUtensorMap &map, const TcArgs &A, size_t smem, int nch, cudaStream_t s) {
-    auto kern = tc_kernel<BF16, MINB>;
+    auto kern = tc_kernel<BF16, G, MINB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)n_tiles(A.g), (unsigned)nch);
-    kern<<<grid, TC_THREADS, smem, s>>>(map, A);
+    kern<<<grid, tc_threads(G), smem, s>>>(map, A);
     return cudaGetLastError();
 }
 
@@ -694,13 +793,16 @@ cudaError_t launch_tc(const TcArgs &args, int bf16, const void *z, int nch, int 
     if (((uintptr_t)z & 15u) != 0) return cudaErrorInvalidValue;
     PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
     if (!encode) return cudaErrorNotSupported;
-    // TMEM columns: accumulator + W stages, a power of two >= 32
-    int cols = 32;
-    while (cols < A.n + TC_SA * TC_ACOLS) cols <<= 1;
-    A.ncols = cols;
+    // CTAs per SM: two while the accumulator leaves room for two W stages in
+    // half of the tensor memory, else one (registers allow at most two).
     int per_sm = ctas_per_sm > 0 ? ctas_per_sm : 2;
-    if (per_sm > 512 / cols) per_sm = 512 / cols;
-    if (per_sm < 1) per_sm = 1;
+    if (per_sm > 2) per_sm = 2;
+    if (per_sm == 2 && A.n + 2 * TC_ACOLS > 256) per_sm = 1;
+    A.ncols = 512 / per_sm;
+    int sa = 1;
+    while (2 * sa <= TC_MAX_SA && A.n + 2 * sa * TC_ACOLS <= A.ncols) sa *= 2;
+    if (sa < 2) return cudaErrorInvalidConfiguration;
+    A.sa = sa;
     const bool has_w = A.w_tx != nullptr;
     const size_t budget = (size_t)(227 * 1024) / per_sm - 1024;  // per-CTA share incl. the runtime's reserve
     const size_t fixed = tc_smem_layout(0, A.n, A.Q, has_w).total;
@@ -711,21 +813,25 @@ cudaError_t launch_tc(const TcArgs &args, int bf16, const void *z, int nch, int 
     A.sb = sbv;
     const size_t smem = tc_smem_layout(sbv, A.n, A.Q, has_w).total;
 
+    // The window of one item is, for every (column group, plane), 16 rows x
+    // 8 values contiguous in memory: the map merges (row, 8 values) into one
+    // 4-D dimension, so a box moves 256-byte runs; its x coordinate 8 k0 is
+    // always 16-byte aligned and rows outside 0 .. K-1 arrive as zeros.
     CUtensorMap map;
     const int QM = A.Q * A.M;
-    const cuuint64_t dims[5] = {8, (cuuint64_t)A.K, 2, (cuuint64_t)(A.n / 8), (cuuint64_t)nch * QM};
-    const cuuint64_t strides[4] = {16, (cuuint64_t)A.K * 16, (cuuint64_t)A.K * 32, (cuuint64_t)(A.n / 8) * A.K * 32};
-    const cuuint32_t box[5] = {8, (cuuint32_t)TC_U, 2, (cuuint32_t)(A.n / 8), 1};
-    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-    const CUresult r = encode(&map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 5,
+    const cuuint64_t dims[4] = {(cuuint64_t)A.K * 8, 2, (cuuint64_t)(A.n / 8), (cuuint64_t)nch * QM};
+    const cuuint64_t strides[3] = {(cuuint64_t)A.K * 16, (cuuint64_t)A.K * 32, (cuuint64_t)(A.n / 8) * A.K * 32};
+    const cuuint32_t box[4] = {(cuuint32_t)TC_U * 8, 2, (cuuint32_t)(A.n / 8), 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = encode(&map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4,
                               const_cast<void *>(z), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
     if (per_sm >= 2) {
-        return bf16 ? launch_tc_t<true, 2>(map, A, smem, nch, s) : launch_tc_t<false, 2>(map, A, smem, nch, s);
+        return bf16 ? launch_tc_t<true, 2, 2>(map, A, smem, nch, s) : launch_tc_t<false, 2, 2>(map, A, smem, nch, s);
     }
-    return bf16 ? launch_tc_t<true, 1>(map, A, smem, nch, s) : launch_tc_t<false, 1>(map, A, smem, nch, s);
+    return bf16 ? launch_tc_t<true, 4, 1>(map, A, smem, nch, s) : launch_tc_t<false, 4, 1>(map, A, smem, nch, s);
 }
 
 }  // namespace das

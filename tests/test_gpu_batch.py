@@ -116,7 +116,11 @@ def test_autotuner_choice_keeps_result(das, tmp_path, monkeypatch):
     for a, b in zip(ref, batch.forward(ys)):
         assert rel_l2(b.cpu().numpy(), a.cpu().numpy()) <= 1e-6
     pr = autotune.tune_plan(plans[0], ys[0], outs[0], reps=1)
-    assert pr["frames_per_thread"] >= 1
+    assert pr["tensor_cores"] or pr["frames_per_thread"] >= 1
+    # whichever kernel won, the plan's image stays within the 16-bit bar
+    x = plans[0].forward(ys[0])
+    plans[0].check()
+    assert rel_l2(x.cpu().numpy(), ref[0].cpu().numpy()) <= 2e-3
     batch.close()
     for p in plans:
         p.close()
