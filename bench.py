@@ -71,7 +71,7 @@ def apply_tuning(plan, args) -> None:
         plan.set_tuning(frames_per_thread=args.fb, staging=args.staging, load_width=args.load_width)
 
 
-def tensor_roofline(plan, items0: int, launches: int, kern_ms: float) -> dict:
+def tensor_roofline(plan, items0: int, launches: int, kern_ms: float, storage: str, profile: str) -> dict:
     """Tensor-pipe roofline of the tcgen05 kernel: MMA flops issued per launch
     (sub-items x 2 x 128 x N x 32, counted by the kernel) over its event time,
     against the measured sustained dense bf16 (= f16) rate."""
@@ -83,30 +83,36 @@ def tensor_roofline(plan, items0: int, launches: int, kern_ms: float) -> dict:
     achieved = flops / (kern_ms * 1e-3) / 1e12
     peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1700.0)))
     return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "tc_kernel (tcgen05 tile contraction)", "kernel_ms": kern_ms,
+            "traffic": profiled_traffic(storage, profile, TC_SOURCES),
+            "kernel": "tc_kernel (tcgen05 tile contraction)", "kernel_ms": kern_ms,
             "peak_source": f"{src} dense bf16 sustained (f16 runs at the same rate)",
             "work_per_launch": f"{items:.0f} MMA sub-items x 128 x {n} x 32 x 2 flop"}
 
 
-def kernel_source_hash() -> str:
+TILE_SOURCES = ("das_tile.cuh", "das_tile_tma.cuh", "das_tile_f32.cu", "das_internal.cuh")
+TC_SOURCES = ("das_tc.cu", "das_tc.cuh", "das_async.cuh", "das_internal.cuh")
+
+
+def kernel_source_hash(files=TILE_SOURCES) -> str:
     h = hashlib.sha1()
-    for f in ("das_tile.cuh", "das_tile_tma.cuh", "das_tile_f32.cu", "das_internal.cuh"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_2606_13259_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
 
 
-def profiled_traffic(storage: str):
-    """DRAM bytes per launch of the tile kernel from the committed ncu summary,
-    if it was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", f"tile_kernel_paper_iq_{storage}.md")
+def profiled_traffic(storage: str, name: str = "tile_kernel_paper_iq", files=TILE_SOURCES):
+    """DRAM bytes per launch of a kernel from its committed ncu summary
+    (profiles/<name>_<storage>.md), if that summary was taken on the current
+    kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", f"{name}_{storage}.md")
     try:
         text = open(path).read()
     except OSError:
         return None
     m = re.search(r"kernel_source_sha1:\s*([0-9a-f]+)", text)
     t = re.search(r"traffic_bytes_per_launch_full:\s*([0-9.eE+]+)", text)
-    if not m or not t or m.group(1) != kernel_source_hash():
+    if not m or not t or m.group(1) != kernel_source_hash(files):
         return None
     return float(t.group(1))
 
@@ -374,7 +380,7 @@ def run_table1(args):
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": args.storage + " storage, f32 arithmetic", "data": "synthetic",
         "config": {"workload": sc.name, "frames_per_step": F, "scene": sc.describe()},
-        "roofline": tensor_roofline(plan, items0, kn, kern_ms) if args.tensor_cores else
+        "roofline": tensor_roofline(plan, items0, kn, kern_ms, args.storage, "tc_kernel_table1") if args.tensor_cores else
         {"bound": "alu", "achieved": flops / (kern_ms * 1e-3) / 1e12, "peak": fp32_peak,
          "unit": "TFLOP/s", "frac": flops / (kern_ms * 1e-3) / 1e12 / fp32_peak, "traffic": None,
          "kernel_ms": kern_ms},
@@ -515,9 +521,11 @@ def main():
     # end to end through the C-ABI with host buffers (copies inside the timed region)
     e2e = None
     if not args.no_e2e:
-        y_host = torch.empty(y.shape, dtype=y.dtype, pin_memory=True)
+        from paper_2606_13259_gb300 import host_empty
+
+        y_host = host_empty(y.shape, y.dtype)  # page-locked huge pages (das_host_alloc)
         y_host.copy_(y)
-        x_host = torch.empty(out.shape, dtype=out.dtype, pin_memory=True)
+        x_host = host_empty(out.shape, out.dtype)
         plan.forward_host(y_host, x_host)
         n_e2e = max(1, min(args.steps, 5))
         if dist:
@@ -549,7 +557,7 @@ def main():
     bytes_store = {"f32": 8, "f16": 4, "bf16": 4, "e4m3": 2}[args.storage]
     alg_bytes = sc.Q * sc.M * sc.K * F * bytes_store + F * sc.N * 8
     if args.tensor_cores:
-        roof = tensor_roofline(plan, items0, kern_n, kern_ms)
+        roof = tensor_roofline(plan, items0, kern_n, kern_ms, args.storage, "tc_kernel_paper_iq")
         roof.update({"useful_flops_tflops": achieved, "hbm_algorithmic_gbs": alg_bytes / (kern_ms * 1e-3) / 1e9})
     else:
         roof = None

@@ -169,9 +169,24 @@ int das_forward(das_plan_t *plan, const void *y_dev, void *x_dev, int batch, das
 
 /* das_forward with host buffers: copies y_host to the device, runs the
  * forward pass and copies the image back into x_host, then synchronises the
- * stream.  Uses device staging buffers the plan reserves on first use
- * (so the first call allocates).  Pinned host memory is fastest. */
+ * stream.  Uses device staging buffers, copy streams and events the plan
+ * creates on first use (so the first call allocates).  Each copy is split
+ * into up to 16 pieces on the plan's own copy streams, ordered with the work
+ * on `stream`.  Pinned host memory is needed for full speed; memory from
+ * das_host_alloc keeps it after long kernels. */
 int das_forward_host(das_plan_t *plan, const void *y_host, void *x_host, int batch, das_stream_t stream);
+
+/* Page-locked host memory for the host calls (no counterpart in the paper):
+ * `bytes` rounded up to whole transparent huge pages, advised as huge pages,
+ * touched and registered with CUDA (cudaHostRegister) for the current
+ * device's context.  Host-to-device copies from small pinned pages lose much
+ * of their speed right after long kernels (the GPU's translations of the host
+ * pages are evicted); huge pages keep the copy at link speed.  Synchronous;
+ * *ptr receives the address (64-byte aligned at least), or NULL on failure.
+ * Free with das_host_free, which accepts only pointers from das_host_alloc
+ * (DAS_ERR_INVALID_ARG otherwise) and NULL. */
+int das_host_alloc(size_t bytes, void **ptr);
+int das_host_free(void *ptr);
 
 /* Adjoint DAS^H: the exact conjugate transpose of the linear map y -> x of
  * das_forward.  x_dev: [batch][N] (float32 / complex64); y_dev: [batch][Q][M][K]

@@ -10,7 +10,7 @@ package only marshals arguments.  Build it with `build.build()`.
 """
 from ._lib import (DAS_STORE_BF16, DAS_STORE_F16, DAS_STORE_F32, DAS_TX_DIVERGING, DAS_TX_NONE, DAS_TX_PLANE,
                    DASError)
-from .plan import Batch, DASFunction, Plan, das
+from .plan import Batch, DASFunction, Plan, das, host_empty
 
-__all__ = ["Plan", "Batch", "DASFunction", "das", "DASError", "DAS_TX_DIVERGING", "DAS_TX_PLANE", "DAS_TX_NONE",
+__all__ = ["Plan", "Batch", "DASFunction", "das", "host_empty", "DASError", "DAS_TX_DIVERGING", "DAS_TX_PLANE", "DAS_TX_NONE",
            "DAS_STORE_F32", "DAS_STORE_F16", "DAS_STORE_BF16"]

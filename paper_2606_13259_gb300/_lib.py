@@ -24,7 +24,7 @@ EXPORTS = ["das_plan_create", "das_plan_destroy", "das_plan_set_c", "das_plan_in
            "das_forward", "das_forward_host", "das_adjoint", "das_grad_c", "das_count_active",
            "das_plan_enable_timing", "das_plan_timing", "das_last_error", "das_version", "das_grad_c_static",
            "das_plan_check", "das_batch_create", "das_batch_forward", "das_batch_set_tuning", "das_batch_info",
-           "das_batch_destroy"]
+           "das_batch_destroy", "das_host_alloc", "das_host_free"]
 
 
 class Geometry(C.Structure):
@@ -115,6 +115,10 @@ def lib():
         L.das_last_error.restype = C.c_char_p
         L.das_version.argtypes = []
         L.das_version.restype = C.c_char_p
+        L.das_host_alloc.argtypes = [C.c_size_t, C.POINTER(vp)]
+        L.das_host_alloc.restype = i
+        L.das_host_free.argtypes = [vp]
+        L.das_host_free.restype = i
         _lib = L
     return _lib
 

@@ -3,17 +3,33 @@
 // kernel dispatch.  See das.h for the contract of every entry point.
 #include "das.h"
 #include "das_internal.cuh"
+#include "das_tc.cuh"
+
+#include <sys/mman.h>
+#include <unistd.h>
 
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
 using namespace das;
 
 static thread_local char g_err[1024];
+
+constexpr int HOST_COPY_STREAMS = 16;
+
+// mappings behind the pointers das_host_alloc returned
+struct HostMap {
+    void *base;
+    size_t len;
+};
+static std::mutex g_host_mutex;
+static std::map<void *, HostMap> g_host_maps;
 
 static int fail(int code, const char *fmt, ...) {
     va_list ap;
@@ -63,6 +79,8 @@ struct das_plan {
     double *scalar = nullptr;
     void *stage_y = nullptr;
     void *stage_x = nullptr;
+    std::vector<cudaStream_t> copy_streams;  // host calls: copies split across these
+    std::vector<cudaEvent_t> copy_events;    // [0] start, [1 + i] end of stream i
     void *z_tc = nullptr;      // tensor-core operand layout of the channel data
     size_t z_tc_bytes = 0;
     float *ratio = nullptr;    // [Q][M] scale / largest scale (tensor-core path)
@@ -350,6 +368,34 @@ int forward_tc(das_plan *p, const void *y, void *x, int B, cudaStream_t s) {
     return DAS_OK;
 }
 
+// Copies `bytes` between host and device as HOST_COPY_STREAMS pieces on the
+// plan's copy streams, ordered after the work already queued on `s` and
+// before what follows on it.  Host pages that the GPU's address translation
+// lost during long kernels are fetched by many copy engines at once instead
+// of one.
+int copy_split(das_plan *p, void *dst, const void *src, size_t bytes, cudaMemcpyKind kind, cudaStream_t s) {
+    const size_t min_piece = (size_t)16 << 20;
+    int pieces = (int)((bytes + min_piece - 1) / min_piece);
+    if (pieces > HOST_COPY_STREAMS) pieces = HOST_COPY_STREAMS;
+    if (pieces <= 1) {
+        DAS_CU(cudaMemcpyAsync(dst, src, bytes, kind, s));
+        return DAS_OK;
+    }
+    const size_t piece = ((bytes + pieces - 1) / pieces + 255) / 256 * 256;
+    DAS_CU(cudaEventRecord(p->copy_events[0], s));
+    for (int i = 0; i < pieces; ++i) {
+        const size_t off = (size_t)i * piece;
+        if (off >= bytes) break;
+        const size_t len = off + piece <= bytes ? piece : bytes - off;
+        cudaStream_t cs = p->copy_streams[i];
+        DAS_CU(cudaStreamWaitEvent(cs, p->copy_events[0], 0));
+        DAS_CU(cudaMemcpyAsync((char *)dst + off, (const char *)src + off, len, kind, cs));
+        DAS_CU(cudaEventRecord(p->copy_events[1 + i], cs));
+        DAS_CU(cudaStreamWaitEvent(s, p->copy_events[1 + i], 0));
+    }
+    return DAS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -550,6 +596,8 @@ void das_plan_destroy(das_plan_t *plan) {
     DeviceGuard guard(plan->device);
     cudaDeviceSynchronize();
     destroy_events(plan);
+    for (cudaStream_t cs : plan->copy_streams) cudaStreamDestroy(cs);
+    for (cudaEvent_t ce : plan->copy_events) cudaEventDestroy(ce);
     for (void *a : plan->allocs) cudaFree(a);
     delete plan;
 }
@@ -698,12 +746,73 @@ int das_forward_host(das_plan_t *plan, const void *y_host, void *x_host, int bat
     const size_t xbytes = (size_t)plan->max_batch * plan->g.n_voxels * sample_bytes_public(plan);
     if (!plan->stage_y && (rc = dalloc(plan, &plan->stage_y, ybytes, "host-call input staging")) != DAS_OK) return rc;
     if (!plan->stage_x && (rc = dalloc(plan, &plan->stage_x, xbytes, "host-call output staging")) != DAS_OK) return rc;
+    if (plan->copy_streams.empty()) {
+        for (int i = 0; i < HOST_COPY_STREAMS; ++i) {
+            cudaStream_t cs;
+            DAS_CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+            plan->copy_streams.push_back(cs);
+        }
+        for (int i = 0; i <= HOST_COPY_STREAMS; ++i) {
+            cudaEvent_t ce;
+            DAS_CU(cudaEventCreateWithFlags(&ce, cudaEventDisableTiming));
+            plan->copy_events.push_back(ce);
+        }
+    }
     const size_t yb = (size_t)batch * plan->Q * plan->M * plan->K * sample_bytes_public(plan);
     const size_t xb = (size_t)batch * plan->g.n_voxels * sample_bytes_public(plan);
-    DAS_CU(cudaMemcpyAsync(plan->stage_y, y_host, yb, cudaMemcpyHostToDevice, s));
+    if ((rc = copy_split(plan, plan->stage_y, y_host, yb, cudaMemcpyHostToDevice, s)) != DAS_OK) return rc;
     if ((rc = das_forward(plan, plan->stage_y, plan->stage_x, batch, stream)) != DAS_OK) return rc;
-    DAS_CU(cudaMemcpyAsync(x_host, plan->stage_x, xb, cudaMemcpyDeviceToHost, s));
+    if ((rc = copy_split(plan, x_host, plan->stage_x, xb, cudaMemcpyDeviceToHost, s)) != DAS_OK) return rc;
     DAS_CU(cudaStreamSynchronize(s));
+    return DAS_OK;
+}
+
+int das_host_alloc(size_t bytes, void **ptr) {
+    g_err[0] = 0;
+    if (!ptr) return fail(DAS_ERR_INVALID_ARG, "ptr is NULL");
+    *ptr = nullptr;
+    if (bytes == 0) return fail(DAS_ERR_INVALID_ARG, "bytes must be > 0");
+    // huge-page size of the kernel (transparent huge pages), 2 MiB if unknown
+    size_t huge = 2u << 20;
+    if (FILE *f = fopen("/sys/kernel/mm/transparent_hugepage/hpage_pmd_size", "r")) {
+        unsigned long long v = 0;
+        if (fscanf(f, "%llu", &v) == 1 && v >= 4096 && (v & (v - 1)) == 0) huge = (size_t)v;
+        fclose(f);
+    }
+    const size_t len = (bytes + huge - 1) / huge * huge;
+    const size_t map_len = len + huge;
+    void *base = mmap(nullptr, map_len, PROT_READ | PROT_WRITE, MAP_PRIVATE | MAP_ANONYMOUS, -1, 0);
+    if (base == MAP_FAILED) return fail(DAS_ERR_OOM, "mmap of %zu bytes failed", map_len);
+    char *p = (char *)(((uintptr_t)base + huge - 1) / huge * huge);
+    madvise(p, len, MADV_HUGEPAGE);  // advisory: small pages still work, only slower after GPU work
+    const long page = sysconf(_SC_PAGESIZE) > 0 ? sysconf(_SC_PAGESIZE) : 4096;
+    for (size_t o = 0; o < len; o += (size_t)page) p[o] = 0;  // fault the pages in before pinning
+    cudaError_t e = cudaHostRegister(p, len, cudaHostRegisterDefault);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        munmap(base, map_len);
+        return cuda_fail(e, "cudaHostRegister");
+    }
+    {
+        std::lock_guard<std::mutex> lock(g_host_mutex);
+        g_host_maps[p] = HostMap{base, map_len};
+    }
+    *ptr = p;
+    return DAS_OK;
+}
+
+int das_host_free(void *ptr) {
+    if (!ptr) return DAS_OK;
+    HostMap m{};
+    {
+        std::lock_guard<std::mutex> lock(g_host_mutex);
+        auto it = g_host_maps.find(ptr);
+        if (it == g_host_maps.end()) return fail(DAS_ERR_INVALID_ARG, "pointer was not returned by das_host_alloc");
+        m = it->second;
+        g_host_maps.erase(it);
+    }
+    cudaHostUnregister(ptr);
+    munmap(m.base, m.len);
     return DAS_OK;
 }
 

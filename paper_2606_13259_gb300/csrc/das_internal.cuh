@@ -125,54 +125,10 @@ struct AdjArgs {
     void *y;             // channel data [B][Q][M][K], public layout
 };
 
-// Arguments of the tensor-core forward kernel (das_tc.cu).
-struct TcArgs {
-    GridDesc g;
-    int M, Q, K;
-    int B;            // frames in this call
-    int bc;           // frames per chunk: MMA columns 0..bc-1 carry real parts, bc..2bc-1 imaginary parts
-    int n;            // MMA N: 2 bc rounded up to a multiple of 16 (<= 256)
-    int sb;           // window stages in shared memory
-    int sa;           // weight stages in tensor memory (power of two)
-    int ncols;        // tensor-memory columns the CTA allocates
-    float a;          // fs / c
-    double ad;
-    float theta, hr, hi, thr, tile_radius;
-    float ahx, ahy, ahz;  // a times the half extents of the tile's voxel-centre box
-    float aR;             // a times the tile radius
-    float aR2h;           // a R^2 / 2
-    const double *elem_pos;
-    const float4 *elem_nrm;
-    const int *tx_tb;
-    const float *tx_t;
-    const float *tx_tmin;
-    const float *tx_tmax;
-    const float *w_tx;
-    const float *ratio;   // [Q][M] storage scale divided by the largest one
-    const float *smax;    // the largest storage scale
-    int *err;             // bit 2: a wait timed out; bit 3: an item needed more windows than a list holds
-    unsigned long long *items;  // running count of MMA sub-items (128 x n x 32 each)
-    float2 *x;            // image [B][N]
-};
-
 // Kernel launchers (defined in the .cu files).
 cudaError_t launch_prepare(const GridDesc &g, int Q, const int *kind, const double *vec, const double *off,
                            const double *t0, double ad, int *tx_tb, float *tx_t, float *tx_tmin, float *tx_tmax,
                            cudaStream_t s);
-// Tensor-core path: channel data y[b][qm][k] (complex64) -> operand layout
-// z[c][qm][n/8][2][K][8] of 16-bit values (see das_tc.cu), the per-(q, m)
-// scale ratios and the largest scale.
-cudaError_t launch_tc_stage(const void *y, void *z, const float2 *rot, const float *scale, const float *inv_scale,
-                            float *ratio, float *smax, int bf16, int B, int bc, int nch, int n, int QM, int K,
-                            cudaStream_t s);
-cudaError_t launch_tc(const TcArgs &args, int bf16, const void *z, int nch, int ctas_per_sm, cudaStream_t s);
-// MMA width and frames per chunk of the tensor-core path for a call of B frames.
-void tc_shape(int B, int &bc, int &nch, int &n);
-// y[b][qm][k] -> z[c][qm][k][fb] with b = c * fb + j; frames B .. nch*fb-1 are zero.
-cudaError_t launch_relayout(const void *y, void *z, const float2 *rot, const float *inv_scale, int iq, int store,
-                            int B, int fb, int nch, int QM, int K, cudaStream_t s);
-cudaError_t launch_scale(const void *y, float *scale, float *inv_scale, int iq, int store, int B, int QM, int K,
-                         cudaStream_t s);
 cudaError_t launch_tile(const TileArgs &args, int mode, int iq, int store, int fb, int n_chunks, cudaStream_t s);
 cudaError_t launch_adjoint(const AdjArgs &args, int iq, cudaStream_t s);
 cudaError_t launch_reduce(const double *partial, long long n, double *out, cudaStream_t s);

@@ -55,7 +55,7 @@
 // of the plan's error word, drains what it has in flight and leaves without
 // writing its image tile.
 #include "das_async.cuh"
-#include "das_internal.cuh"
+#include "das_tc.cuh"
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -71,8 +71,7 @@ constexpr int TC_U = 16;        // window rows per sub-item
 constexpr int TC_KV = TC_U - 1; // values of k a sub-item covers
 constexpr int TC_MAX_SA = 16;   // W stages in TMEM (power of two, set per launch)
 constexpr int TC_ACOLS = 16;    // TMEM columns per W stage
-constexpr int TC_EB = 256;           // element records per block
-constexpr int TC_LIST = 4096;        // sub-items per list round
+constexpr int TC_LIST_MAX = 4096;    // sub-items per list round (largest list)
 constexpr int TC_MAX_SB = 24;
 constexpr float TC_MARGIN = 0.02f;  // samples
 
@@ -248,18 +247,20 @@ struct TcSmem {
     size_t bars, misc, list, lw, eg, en, gb, erb, em, t, w, tb, tmin, tmax, total;
 };
 
-__host__ __device__ inline TcSmem tc_smem_layout(int sb, int n, int Q, bool has_w) {
+// Shared memory of one CTA: sb window stages, barriers, the element records
+// of one block of eb elements and a sub-item list of list_cap entries.
+__host__ __device__ inline TcSmem tc_smem_layout(int sb, int n, int Q, bool has_w, int eb, int list_cap) {
     TcSmem L{};
     size_t o = (size_t)sb * 64 * n;  // window stages (1024-aligned base)
     L.bars = o; o += 128 * 8;
-    L.misc = o; o += 32 * 4;
-    L.list = o; o += (size_t)TC_LIST * 8;
-    L.lw = o; o += (size_t)TC_LIST * 4;
-    L.eg = o; o += (size_t)TC_EB * 16;
-    L.en = o; o += (size_t)TC_EB * 16;
-    L.gb = o; o += (size_t)TC_EB * 8;
-    L.erb = o; o += (size_t)TC_EB * 4;
-    L.em = o; o += (size_t)TC_EB * 4;
+    L.misc = o; o += 64 * 4;
+    L.list = o; o += (size_t)list_cap * 8;
+    L.lw = o; o += (size_t)list_cap * 4;
+    L.eg = o; o += (size_t)eb * 16;
+    L.en = o; o += (size_t)eb * 16;
+    L.gb = o; o += (size_t)eb * 8;
+    L.erb = o; o += (size_t)eb * 4;
+    L.em = o; o += (size_t)eb * 4;
     L.t = o; o += (size_t)Q * TILE_N * 4;
     L.w = o; o += has_w ? (size_t)Q * TILE_N * 4 : 0;
     L.tb = o; o += (size_t)Q * 4;
@@ -271,18 +272,20 @@ __host__ __device__ inline TcSmem tc_smem_layout(int sb, int n, int Q, bool has_
 
 // misc words of the kernel's shared memory
 enum : int { MW_TMEM = 0, MW_ABORT = 1, MW_ISSUED = 2, MW_NEL = 3, MW_NLIST = 4, MW_NEXT = 5, MW_CNT = 8,
-             MW_SCAN = 16 };
+             MW_SCAN = 32 };
 
 template <bool BF16, int G, int MINB>
 __global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_constant__ CUtensorMap zmap,
                                                                  const __grid_constant__ TcArgs A) {
     constexpr int NB = G * TILE_N;  // builder threads
+    constexpr int EB = NB;          // element records per block (one element per builder thread)
+    const int list_cap = A.list_cap;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
     const int Q = A.Q, M = A.M, K = A.K, n = A.n, sb = A.sb;
     const uint32_t sa_n = (uint32_t)A.sa, sa_shift = (uint32_t)(31 - __clz(A.sa));
     const bool has_w = A.w_tx != nullptr;
-    const TcSmem L = tc_smem_layout(sb, n, Q, has_w);
+    const TcSmem L = tc_smem_layout(sb, n, Q, has_w, EB, list_cap);
     const uint32_t stage_bytes = 64u * (uint32_t)n;
     unsigned char *sB = smem;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L.bars);
@@ -363,8 +366,8 @@ __global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_co
     bool stop = misc[MW_ABORT] != 0u;
     uint32_t tma_issued = 0;  // producer: window copies issued
 
-    for (int m0 = 0; m0 < M; m0 += TC_EB) {
-        const int mend = min(M, m0 + TC_EB);
+    for (int m0 = 0; m0 < M; m0 += EB) {
+        const int mend = min(M, m0 + EB);
         // ---- compaction of the candidate elements of this block (builder threads) ----
         {
             bool cand = false;
@@ -372,7 +375,7 @@ __global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_co
             float2 gbv = make_float2(0.f, 0.f);
             int rb = 0;
             const int m = m0 + tid;
-            if (tid < TC_EB && m < mend) {
+            if (tid < EB && m < mend) {
                 const double rx = A.elem_pos[3 * m], ry = A.elem_pos[3 * m + 1], rz = A.elem_pos[3 * m + 2];
                 const double Gx = p0x - rx, Gy = p0y - ry, Gz = p0z - rz;
                 const double D0 = sqrt(Gx * Gx + Gy * Gy + Gz * Gz);
@@ -382,10 +385,12 @@ __global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_co
                 const float4 nn = A.elem_nrm[m];
                 eg = make_float4((float)Gx, (float)Gy, (float)Gz, (float)D0);
                 en = make_float4(nn.x, nn.y, nn.z, (float)(R0 - Rf));
-                if (D0 > 1e-12) {
-                    const double ux = Gx / D0, uy = Gy / D0, uz = Gz / D0;
-                    const float lin = (float)(fabs(ux) * A.ahx + fabs(uy) * A.ahy + fabs(uz) * A.ahz);
-                    const float curv = (float)(A.aR2h / D0);
+                if (eg.w > 1e-12f) {
+                    // window bound offsets in float32 (0.02-sample margin); the
+                    // reference delay above stays float64
+                    const float inv = 1.f / eg.w;
+                    const float lin = (fabsf(eg.x) * A.ahx + fabsf(eg.y) * A.ahy + fabsf(eg.z) * A.ahz) * inv;
+                    const float curv = A.aR2h * inv;
                     gbv = make_float2(-lin - TC_MARGIN, fminf(lin + curv, A.aR) + TC_MARGIN);
                 } else {
                     gbv = make_float2(-A.aR - TC_MARGIN, A.aR + TC_MARGIN);
@@ -402,9 +407,9 @@ __global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_co
                 }
             }
             const unsigned bal = __ballot_sync(0xffffffffu, cand);
-            if (tid < TC_EB && lane == 0) misc[MW_CNT + warp] = __popc(bal);
+            if (tid < EB && lane == 0) misc[MW_CNT + warp] = __popc(bal);
             __syncthreads();
-            if (tid < TC_EB && cand) {
+            if (tid < EB && cand) {
                 int off = 0;
                 for (int w = 0; w < warp; ++w) off += (int)misc[MW_CNT + w];
                 const int idx = off + __popc(bal & ((1u << lane) - 1u));
@@ -416,7 +421,7 @@ __global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_co
             }
             if (tid == 0) {
                 int tot = 0;
-                for (int w = 0; w < TC_EB / 32; ++w) tot += (int)misc[MW_CNT + w];
+                for (int w = 0; w < EB / 32; ++w) tot += (int)misc[MW_CNT + w];
                 misc[MW_NEL] = (uint32_t)tot;
             }
             __syncthreads();
@@ -455,14 +460,14 @@ __global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_co
                     const int j = p / Q, q = p - j * Q;
                     int klo;
                     int ns = tc_item(s_tb[q], s_erb[j], s_en[j].w, s_tmin[q], s_tmax[q], s_gb[j], K, klo);
-                    if (off + ns > TC_LIST) {
-                        if (ns > TC_LIST) {  // one pair wider than the whole list: keep what fits, flag it
+                    if (off + ns > list_cap) {
+                        if (ns > list_cap) {  // one pair wider than the whole list: keep what fits, flag it
                             if (off == 0) {
                                 atomicOr(A.err, 8);
-                                ns = TC_LIST;
+                                ns = list_cap;
                             }
                         }
-                        if (off + ns > TC_LIST) {
+                        if (off + ns > list_cap) {
                             atomicMin(&misc[MW_NEXT], (uint32_t)p);
                             break;
                         }
@@ -804,14 +809,21 @@ cudaError_t launch_tc(const TcArgs &args, int bf16, const void *z, int nch, int 
     if (sa < 2) return cudaErrorInvalidConfiguration;
     A.sa = sa;
     const bool has_w = A.w_tx != nullptr;
+    const int G = per_sm >= 2 ? 2 : 4;
+    const int eb = G * TILE_N;
+    // a list holds every sub-item of a block when no item needs two windows
+    long long cap = (long long)eb * A.Q;
+    if (cap < 256) cap = 256;
+    if (cap > TC_LIST_MAX) cap = TC_LIST_MAX;
+    A.list_cap = (int)cap;
     const size_t budget = (size_t)(227 * 1024) / per_sm - 1024;  // per-CTA share incl. the runtime's reserve
-    const size_t fixed = tc_smem_layout(0, A.n, A.Q, has_w).total;
+    const size_t fixed = tc_smem_layout(0, A.n, A.Q, has_w, eb, A.list_cap).total;
     const size_t stage = (size_t)64 * A.n;
     int sbv = fixed < budget ? (int)((budget - fixed) / stage) : 0;
     if (sbv > TC_MAX_SB) sbv = TC_MAX_SB;
     if (sbv < 2) return cudaErrorInvalidConfiguration;
     A.sb = sbv;
-    const size_t smem = tc_smem_layout(sbv, A.n, A.Q, has_w).total;
+    const size_t smem = tc_smem_layout(sbv, A.n, A.Q, has_w, eb, A.list_cap).total;
 
     // The window of one item is, for every (column group, plane), 16 rows x
     // 8 values contiguous in memory: the map merges (row, 8 values) into one

@@ -179,12 +179,13 @@ class Plan:
         return out
 
     def forward_host(self, y: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
-        """Host tensors in and out (copies inside the library call)."""
+        """Host tensors in and out (copies inside the library call).  Buffers from
+        host_empty keep the copies at link speed after long kernels."""
         if y.device.type != "cpu" or not y.is_contiguous() or y.dtype != self.data_dtype:
             raise ValueError("y must be a contiguous CPU tensor of the plan's data type")
         B = y.shape[0]
         if out is None:
-            out = torch.empty((B,) + self.shape, dtype=self.data_dtype, pin_memory=True)
+            out = host_empty((B,) + self.shape, self.data_dtype)
         L.check(self._lib.das_forward_host(self._h, _ptr(y), _ptr(out), B, _stream(stream)))
         return out
 
@@ -214,6 +215,37 @@ class Plan:
         n = C.c_longlong()
         L.check(self._lib.das_count_active(self._h, C.byref(n), _stream(stream)))
         return int(n.value)
+
+
+class _HostBlock:
+    """Owner of one das_host_alloc block; numpy keeps it alive through the
+    array interface for as long as any view of the memory exists."""
+
+    def __init__(self, nbytes: int):
+        self._lib = L.lib()
+        ptr = C.c_void_p()
+        L.check(self._lib.das_host_alloc(C.c_size_t(nbytes), C.byref(ptr)))
+        self.ptr = ptr.value
+        self.__array_interface__ = {"data": (self.ptr, False), "shape": (nbytes,), "typestr": "|u1", "version": 3}
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            self._lib.das_host_free(C.c_void_p(self.ptr))
+            self.ptr = None
+
+
+def host_empty(shape, dtype: torch.dtype) -> torch.Tensor:
+    """A CPU tensor in page-locked huge-page memory (das_host_alloc), the
+    fastest host buffer for Plan.forward_host; freed with its last view."""
+    import numpy as np
+
+    shape = tuple(int(s) for s in shape)
+    n = 1
+    for s in shape:
+        n *= s
+    nbytes = max(1, n * torch.empty((), dtype=dtype).element_size())
+    block = np.asarray(_HostBlock(nbytes))
+    return torch.from_numpy(block).view(dtype)[:n].view(shape)
 
 
 class DASFunction(torch.autograd.Function):

@@ -88,3 +88,21 @@ def test_null_arguments_rejected(lib):
     assert L.das_grad_c(None, None, None, None, 1, None) == lib.DAS_ERR_INVALID_ARG
     assert L.das_plan_set_c(None, 1500.0) == lib.DAS_ERR_INVALID_ARG
     L.das_plan_destroy(None)
+
+
+def test_host_allocator_arguments(lib):
+    """das_host_alloc / das_host_free reject bad arguments; without a GPU the
+    registration fails cleanly (with one, the block is returned and freed)."""
+    L = lib.lib()
+    ptr = C.c_void_p()
+    assert L.das_host_alloc(C.c_size_t(0), C.byref(ptr)) == lib.DAS_ERR_INVALID_ARG
+    assert L.das_host_alloc(C.c_size_t(1 << 20), None) == lib.DAS_ERR_INVALID_ARG
+    assert L.das_host_free(None) == lib.DAS_OK
+    junk = (C.c_char * 64)()
+    assert L.das_host_free(C.cast(junk, C.c_void_p)) == lib.DAS_ERR_INVALID_ARG
+    rc = L.das_host_alloc(C.c_size_t(1 << 20), C.byref(ptr))
+    if rc == lib.DAS_OK:
+        assert ptr.value and ptr.value % 64 == 0
+        assert L.das_host_free(ptr) == lib.DAS_OK
+    else:
+        assert rc == lib.DAS_ERR_CUDA and not ptr.value

@@ -203,3 +203,37 @@ def test_staged_paper_tile_geometry_small_batch(das, oracle):
     plan.close()
     ref = oracle.forward(sc, y.cpu().numpy())
     assert rel_l2(x, ref) <= TOL_F32
+
+
+@pytest.mark.parametrize("kind", ["huge_pages", "pinned", "pageable"])
+def test_forward_host_matches_device_call(das, kind):
+    """Host buffers in, host buffers out (copies split across the plan's copy
+    streams): the same image as the device call, for huge-page buffers from
+    das_host_alloc, torch-pinned and plain pageable memory."""
+    sc = ragged_scene(*RAGGED[0])
+    B = 5
+    y = S.random_channels(sc, B, seed=12)
+    plan = das.Plan.from_scene(sc, max_batch=B)
+    ref = plan.forward(y.cuda()).cpu()
+    if kind == "huge_pages":
+        yh, xh = das.host_empty(y.shape, y.dtype), das.host_empty(ref.shape, ref.dtype)
+        assert yh.is_pinned() and xh.is_pinned()
+    elif kind == "pinned":
+        yh, xh = torch.empty(y.shape, dtype=y.dtype).pin_memory(), torch.empty(ref.shape, dtype=ref.dtype).pin_memory()
+    else:
+        yh, xh = torch.empty(y.shape, dtype=y.dtype), torch.empty(ref.shape, dtype=ref.dtype)
+    yh.copy_(y)
+    plan.forward_host(yh, xh)
+    plan.close()
+    assert torch.equal(xh, ref)
+
+
+def test_host_empty_large_block_round_trip(das):
+    """A block larger than one huge page survives a device round trip."""
+    n = 3 * (1 << 27) + 12345  # ~ 1.5 GB of uint8 spread over several huge pages
+    h = das.host_empty((n,), torch.uint8)
+    h[:: 1 << 20] = 7
+    d = h.cuda()
+    back = das.host_empty((n,), torch.uint8)
+    back.copy_(d)
+    assert torch.equal(back[:: 1 << 20], h[:: 1 << 20])
