@@ -12,12 +12,18 @@
 //
 // Delays use the same split as the forward kernels (float64 reference to the
 // tile centre, float32 offsets; see das_internal.cuh).
+//
+// A thread owns one line of 8 voxels along x in a tile (16 lines per tile,
+// 32 tiles in flight per CTA).  For each transmit it walks the line keeping
+// the contributions to two consecutive sample rows in registers; neighbours
+// along x mostly fall on the same or the next row, so a row is added to shared
+// memory (one atomic per value) only when the walk leaves it, instead of once
+// per voxel.
 #include "das_internal.cuh"
 
 namespace das {
 
-constexpr int ADJ_SLOTS = 4;                 // tiles processed at once
-constexpr int ADJ_THREADS = ADJ_SLOTS * TILE_N;
+constexpr int ADJ_THREADS = 512;  // 32 tiles x 16 voxel lines in flight per CTA
 
 struct AdjTileRec {
     float gx, gy, gz, d0;  // tile centre minus element, and its norm
@@ -49,23 +55,13 @@ __global__ void __launch_bounds__(ADJ_THREADS, 2) adjoint_kernel(const AdjArgs A
     const float4 nn = A.elem_nrm[m];
     const long long ntiles = n_tiles(g);
 
-    // Threads 128 s .. 128 s + 127 take the tile in slot s; within it warp w
-    // holds the voxels of row y = w, lane l the voxel x = l % 8, z = l / 8.  A
-    // warp then stays inside one tile (coherent aperture decisions) and its
-    // lanes at different depths add into different sample rows; only the x
-    // neighbours at one depth can meet on a row.
-    const int slot = tid / TILE_N;
-    const int lx = tid & 7, ly = (tid >> 5) & 3, lz = (tid >> 3) & 3;
-    int vl = 0;  // tile lane of voxel (lx, ly, lz): index of the per-voxel transmit tables
-    for (int c = 0; c < TILE_N; ++c) {
-        int cx, cy, cz;
-        lane_offset(c, cx, cy, cz);
-        if (cx == lx && cy == ly && cz == lz) vl = c;
-    }
-    const float dx = (float)(g.sx * (lx - 0.5 * (TILE_X - 1)));
+    // Thread = (tile slot, line): slot tid / 16 takes every 32nd candidate
+    // tile, line tid % 16 the voxels (x = 0..7, y = line % 4, z = line / 4).
+    const int slot = tid >> 4;
+    const int line = tid & 15;
+    const int ly = line & 3, lz = line >> 2;
     const float dy = (float)(g.sy * (ly - 0.5 * (TILE_Y - 1)));
     const float dz = (float)(g.sz * (lz - 0.5 * (TILE_Z - 1)));
-    const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
 
     for (long long t0 = 0; t0 < ntiles; t0 += ADJ_THREADS) {
         __syncthreads();  // records of the previous pass are no longer read (and acc is zeroed)
@@ -112,77 +108,122 @@ __global__ void __launch_bounds__(ADJ_THREADS, 2) adjoint_kernel(const AdjArgs A
         if (cand) recs[off + __popc(bal & ((1u << lane) - 1u))] = rec;
         __syncthreads();
 
-        // Each slot takes a contiguous quarter of the candidate list (tiles are
-        // listed x-fastest), so the tiles in flight together lie at different
-        // depths and their lanes add into different sample rows.
-        const int per = (total + ADJ_SLOTS - 1) / ADJ_SLOTS;
-        const int c_end = min(total, (slot + 1) * per);
-        for (int c = slot * per; c < c_end; ++c) {
+        for (int c = slot; c < total; c += ADJ_THREADS / 16) {
             const AdjTileRec R = recs[c];
             const int tile = R.tile;
             const int tx = tile % g.tiles_x;
             const int ty = (tile / g.tiles_x) % g.tiles_y;
             const int tz = tile / (g.tiles_x * g.tiles_y);
-            const int ix = tx * TILE_X + lx, iy = ty * TILE_Y + ly, iz = tz * TILE_Z + lz;
-            if (ix >= g.nx || iy >= g.ny || iz >= g.nz) continue;
-            const float ex = R.gx + dx, ey = R.gy + dy, ez = R.gz + dz;
-            if (A.thr >= 0.f) {
-                const float zax = fmaf(ex, nn.x, fmaf(ey, nn.y, ez * nn.z));
-                const float ux = fmaf(ey, nn.z, -ez * nn.y), uy = fmaf(ez, nn.x, -ex * nn.z),
-                            uz = fmaf(ex, nn.y, -ey * nn.x);
-                const float rho2 = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
-                if (!((zax > 0.f) && (rho2 <= A.thr * zax * zax))) continue;
-            }
-            const long long n = ((long long)iz * g.ny + iy) * g.nx + ix;
-            const float d = sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
-            const float num = fmaf(2.f, fmaf(R.gx, dx, fmaf(R.gy, dy, R.gz * dz)), dd);
-            const float r = R.rf + A.a * __fdividef(num, d + R.d0);
-            float xr[FB], xi[FB];
+            const int iy = ty * TILE_Y + ly, iz = tz * TILE_Z + lz;
+            if (iy >= g.ny || iz >= g.nz) continue;
+            // receive geometry of the 8 voxels of the line (transmit independent)
+            float r[TILE_X];
+            unsigned live = 0u;  // bit x: voxel inside the grid and the aperture
 #pragma unroll
-            for (int b = 0; b < FB; ++b) {
-                xr[b] = xi[b] = 0.f;
-                if (b0 + b < A.B) {
-                    const size_t o = (size_t)(b0 + b) * g.n_voxels + n;
-                    if (IQ) {
-                        const float2 v = reinterpret_cast<const float2 *>(A.x)[o];
-                        xr[b] = v.x; xi[b] = v.y;
-                    } else {
-                        xr[b] = reinterpret_cast<const float *>(A.x)[o];
-                    }
+            for (int x = 0; x < TILE_X; ++x) {
+                const float dx = (float)(g.sx * (x - 0.5 * (TILE_X - 1)));
+                const float ex = R.gx + dx, ey = R.gy + dy, ez = R.gz + dz;
+                bool in = tx * TILE_X + x < g.nx;
+                if (A.thr >= 0.f) {
+                    const float zax = fmaf(ex, nn.x, fmaf(ey, nn.y, ez * nn.z));
+                    const float ux = fmaf(ey, nn.z, -ez * nn.y), uy = fmaf(ez, nn.x, -ex * nn.z),
+                                uz = fmaf(ex, nn.y, -ey * nn.x);
+                    const float rho2 = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
+                    in = in && (zax > 0.f) && (rho2 <= A.thr * zax * zax);
                 }
+                const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                const float d = sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
+                const float num = fmaf(2.f, fmaf(R.gx, dx, fmaf(R.gy, dy, R.gz * dz)), dd);
+                r[x] = R.rf + A.a * __fdividef(num, d + R.d0);
+                live |= (in ? 1u : 0u) << x;
             }
+            if (live == 0u) continue;
+            const long long nrow = ((long long)iz * g.ny + iy) * g.nx + (long long)tx * TILE_X;
             for (int qq = 0; qq < nq; ++qq) {
                 const int q = q0 + qq;
                 const size_t tq = (size_t)tile * A.Q + q;
-                const float f = r + __ldg(A.tx_t + tq * TILE_N + vl);
-                const float fl = floorf(f);
-                const float al = f - fl;
-                const int k = __ldg(A.tx_tb + tq) + R.rb + (int)fl;
-                if ((unsigned)k > (unsigned)(K - 2)) continue;
-                const float w = A.w_tx ? __ldg(A.w_tx + tq * TILE_N + vl) : 1.f;
-                float *a0 = acc + ((size_t)qq * K + k) * FB * C;
-                float *a1 = a0 + FB * C;
-                if constexpr (IQ) {
-                    float sn, cs;
-                    __sincosf(A.theta * (al - 0.5f), &sn, &cs);
-                    const float uhr = cs * A.hr - sn * A.hi, uhi = cs * A.hi + sn * A.hr;
-                    const float ubr = cs * A.hr + sn * A.hi, ubi = sn * A.hr - cs * A.hi;
-                    const float w0 = w * (1.f - al), w1 = w * al;
-                    // conjugated coefficients of the two taps (pre-rotated sample domain)
-                    const float c0r = w0 * uhr, c0i = -w0 * uhi, c1r = w1 * ubr, c1i = -w1 * ubi;
+                const int kb = __ldg(A.tx_tb + tq) + R.rb;
+                float* const arow = acc + (size_t)qq * K * FB * C;
+                // running rows kc and kc + 1 (kc = -4: none yet)
+                int kc = -4;
+                float a0[FB * C], a1[FB * C];
 #pragma unroll
-                    for (int b = 0; b < FB; ++b) {
-                        atomicAdd(a0 + 2 * b, c0r * xr[b] - c0i * xi[b]);
-                        atomicAdd(a0 + 2 * b + 1, c0r * xi[b] + c0i * xr[b]);
-                        atomicAdd(a1 + 2 * b, c1r * xr[b] - c1i * xi[b]);
-                        atomicAdd(a1 + 2 * b + 1, c1r * xi[b] + c1i * xr[b]);
+                for (int i = 0; i < FB * C; ++i) a0[i] = a1[i] = 0.f;
+#pragma unroll
+                for (int x = 0; x < TILE_X; ++x) {
+                    if (!((live >> x) & 1u)) continue;
+                    // tile lane of voxel (x, ly, lz) (inverse of lane_offset)
+                    const int vl = ((x & 3) | ((ly & 1) << 2)) | (((x >> 2) | ((ly >> 1) << 1)) << 3) | (lz << 5);
+                    const float f = r[x] + __ldg(A.tx_t + tq * TILE_N + vl);
+                    const float fl = floorf(f);
+                    const float al = f - fl;
+                    const int k = kb + (int)fl;
+                    if ((unsigned)k > (unsigned)(K - 2)) continue;
+                    const float w = A.w_tx ? __ldg(A.w_tx + tq * TILE_N + vl) : 1.f;
+                    float c0r, c0i = 0.f, c1r, c1i = 0.f;
+                    if constexpr (IQ) {
+                        float sn, cs;
+                        __sincosf(A.theta * (al - 0.5f), &sn, &cs);
+                        const float uhr = cs * A.hr - sn * A.hi, uhi = cs * A.hi + sn * A.hr;
+                        const float ubr = cs * A.hr + sn * A.hi, ubi = sn * A.hr - cs * A.hi;
+                        const float w0 = w * (1.f - al), w1 = w * al;
+                        // conjugated coefficients of the two taps (pre-rotated sample domain)
+                        c0r = w0 * uhr; c0i = -w0 * uhi; c1r = w1 * ubr; c1i = -w1 * ubi;
+                    } else {
+                        c0r = w * (1.f - al);
+                        c1r = w * al;
                     }
-                } else {
-                    const float w0 = w * (1.f - al), w1 = w * al;
+                    // rows kc, kc + 1 that the new pair (k, k + 1) no longer covers go to shared memory
+                    const bool keep0 = kc == k || kc == k + 1;
+                    const bool keep1 = kc + 1 == k || kc + 1 == k + 1;
+                    if (kc >= 0 && !keep0) {
+                        float *p = arow + (size_t)kc * FB * C;
+#pragma unroll
+                        for (int i = 0; i < FB * C; ++i) atomicAdd(p + i, a0[i]);
+                    }
+                    if (kc >= 0 && !keep1) {
+                        float *p = arow + (size_t)(kc + 1) * FB * C;
+#pragma unroll
+                        for (int i = 0; i < FB * C; ++i) atomicAdd(p + i, a1[i]);
+                    }
+                    // carry what stays into the new pair's slots
+                    float n0[FB * C], n1[FB * C];
+#pragma unroll
+                    for (int i = 0; i < FB * C; ++i) {
+                        n0[i] = kc == k ? a0[i] : (kc + 1 == k ? a1[i] : 0.f);
+                        n1[i] = kc == k + 1 ? a0[i] : (kc == k ? a1[i] : 0.f);
+                    }
+                    kc = k;
 #pragma unroll
                     for (int b = 0; b < FB; ++b) {
-                        atomicAdd(a0 + b, w0 * xr[b]);
-                        atomicAdd(a1 + b, w1 * xr[b]);
+                        float xr = 0.f, xi = 0.f;
+                        if (b0 + b < A.B) {
+                            const size_t o = (size_t)(b0 + b) * g.n_voxels + nrow + x;
+                            if constexpr (IQ) {
+                                const float2 v = __ldg(reinterpret_cast<const float2 *>(A.x) + o);
+                                xr = v.x;
+                                xi = v.y;
+                            } else {
+                                xr = __ldg(reinterpret_cast<const float *>(A.x) + o);
+                            }
+                        }
+                        if constexpr (IQ) {
+                            a0[2 * b] = n0[2 * b] + (c0r * xr - c0i * xi);
+                            a0[2 * b + 1] = n0[2 * b + 1] + (c0r * xi + c0i * xr);
+                            a1[2 * b] = n1[2 * b] + (c1r * xr - c1i * xi);
+                            a1[2 * b + 1] = n1[2 * b + 1] + (c1r * xi + c1i * xr);
+                        } else {
+                            a0[b] = n0[b] + c0r * xr;
+                            a1[b] = n1[b] + c1r * xr;
+                        }
+                    }
+                }
+                if (kc >= 0) {
+                    float *p = arow + (size_t)kc * FB * C;
+#pragma unroll
+                    for (int i = 0; i < FB * C; ++i) {
+                        atomicAdd(p + i, a0[i]);
+                        atomicAdd(p + FB * C + i, a1[i]);
                     }
                 }
             }
