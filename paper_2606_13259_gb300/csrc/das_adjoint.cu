@@ -139,6 +139,27 @@ __global__ void __launch_bounds__(ADJ_THREADS, 2) adjoint_kernel(const AdjArgs A
             }
             if (live == 0u) continue;
             const long long nrow = ((long long)iz * g.ny + iy) * g.nx + (long long)tx * TILE_X;
+            // with one frame per CTA the line's image values stay in registers across transmits
+            constexpr bool HOIST = FB == 1;
+            float xh[HOIST ? TILE_X * C : 1];
+            if constexpr (HOIST) {
+#pragma unroll
+                for (int x = 0; x < TILE_X; ++x) {
+                    float xr = 0.f, xi = 0.f;
+                    if (((live >> x) & 1u) && b0 < A.B) {
+                        const size_t o = (size_t)b0 * g.n_voxels + nrow + x;
+                        if constexpr (IQ) {
+                            const float2 v = __ldg(reinterpret_cast<const float2 *>(A.x) + o);
+                            xr = v.x;
+                            xi = v.y;
+                        } else {
+                            xr = __ldg(reinterpret_cast<const float *>(A.x) + o);
+                        }
+                    }
+                    xh[x * C] = xr;
+                    if constexpr (IQ) xh[x * C + 1] = xi;
+                }
+            }
             for (int qq = 0; qq < nq; ++qq) {
                 const int q = q0 + qq;
                 const size_t tq = (size_t)tile * A.Q + q;
@@ -197,7 +218,10 @@ __global__ void __launch_bounds__(ADJ_THREADS, 2) adjoint_kernel(const AdjArgs A
 #pragma unroll
                     for (int b = 0; b < FB; ++b) {
                         float xr = 0.f, xi = 0.f;
-                        if (b0 + b < A.B) {
+                        if constexpr (HOIST) {
+                            xr = xh[x * C];
+                            if constexpr (IQ) xi = xh[x * C + 1];
+                        } else if (b0 + b < A.B) {
                             const size_t o = (size_t)(b0 + b) * g.n_voxels + nrow + x;
                             if constexpr (IQ) {
                                 const float2 v = __ldg(reinterpret_cast<const float2 *>(A.x) + o);
