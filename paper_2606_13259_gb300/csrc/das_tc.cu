@@ -73,6 +73,7 @@ constexpr int TC_MAX_SA = 16;   // W stages in TMEM (power of two, set per launc
 constexpr int TC_ACOLS = 16;    // TMEM columns per W stage
 constexpr int TC_LIST_MAX = 4096;    // sub-items per list round (largest list)
 constexpr int TC_MAX_SB = 24;
+constexpr int TC_PRODUCERS = 4;  // producer lanes issuing window copies
 constexpr float TC_MARGIN = 0.02f;  // samples
 
 // ---------------------------------------------------------------------------
@@ -253,7 +254,7 @@ __host__ __device__ inline TcSmem tc_smem_layout(int sb, int n, int Q, bool has_
     TcSmem L{};
     size_t o = (size_t)sb * 64 * n;  // window stages (1024-aligned base)
     L.bars = o; o += 128 * 8;
-    L.misc = o; o += 64 * 4;
+    L.misc = o; o += 128 * 4;
     L.list = o; o += (size_t)list_cap * 8;
     L.lw = o; o += (size_t)list_cap * 4;
     L.eg = o; o += (size_t)eb * 16;
@@ -272,7 +273,7 @@ __host__ __device__ inline TcSmem tc_smem_layout(int sb, int n, int Q, bool has_
 
 // misc words of the kernel's shared memory
 enum : int { MW_TMEM = 0, MW_ABORT = 1, MW_ISSUED = 2, MW_NEL = 3, MW_NLIST = 4, MW_NEXT = 5, MW_CNT = 8,
-             MW_SCAN = 32 };
+             MW_SCAN = 40 };  // MW_CNT, MW_SCAN: one word per builder warp (up to 32)
 
 template <bool BF16, int G, int MINB>
 __global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_constant__ CUtensorMap zmap,
@@ -365,6 +366,9 @@ __global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_co
     const size_t qm_base = (size_t)chunk * Q * M;
     bool stop = misc[MW_ABORT] != 0u;
     uint32_t tma_issued = 0;  // producer: window copies issued
+    // position in the window ring of this thread's role (producer, MMA
+    // issuer): slot, completed passes over the ring (its low bit is the phase)
+    uint32_t b_slot = (warp == NB / 32 && lane < TC_PRODUCERS) ? (uint32_t)lane : 0u, b_pass = 0;
 
     for (int m0 = 0; m0 < M; m0 += EB) {
         const int mend = min(M, m0 + EB);
@@ -569,44 +573,58 @@ __global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_co
                 __syncwarp();
                 mbar_arrive_if(&fullA[pend_sa], pending && lane == 0);
             } else if (warp == NB / 32) {
-                // ---- producer: window copies ----
-                if (lane == 0) {
-                    for (int e = 0; e < n_list && !stop; ++e) {
+                // ---- producer: window copies, TC_PRODUCERS lanes; lane L takes the
+                // sub-items with global index = L mod TC_PRODUCERS, whose ring slots
+                // are = L mod TC_PRODUCERS (the stage count is a multiple of it) ----
+                if (lane < TC_PRODUCERS) {
+                    for (int e = (int)(((uint32_t)lane + TC_PRODUCERS - base % TC_PRODUCERS) % TC_PRODUCERS);
+                         e < n_list && !stop; e += TC_PRODUCERS) {
                         const uint32_t gi = base + (uint32_t)e;
                         const int2 ent = s_list[e];
                         const int j = ent.y & 511, q = (ent.y >> 9) & 127;
-                        const uint32_t slot = gi % (uint32_t)sb, use = gi / (uint32_t)sb;
-                        if (use > 0 && !tc_wait(&emptyB[slot], (use - 1) & 1u, s_abort, A.err)) {
+                        if (b_pass > 0 && !tc_wait(&emptyB[b_slot], (b_pass - 1) & 1u, s_abort, A.err)) {
                             stop = true;
                             break;
                         }
-                        mbar_arrive_expect_tx(&fullB[slot], stage_bytes);
-                        tma_load_4d(sB + (size_t)slot * stage_bytes, &zmap, 8 * ent.x, 0, 0,
-                                    (int)(qm_base + (size_t)q * M + s_em[j]), &fullB[slot]);
+                        mbar_arrive_expect_tx(&fullB[b_slot], stage_bytes);
+                        tma_load_4d(sB + (size_t)b_slot * stage_bytes, &zmap, 8 * ent.x, 0, 0,
+                                    (int)(qm_base + (size_t)q * M + s_em[j]), &fullB[b_slot]);
                         tma_issued = gi + 1u;
+                        b_slot += TC_PRODUCERS;
+                        if (b_slot >= (uint32_t)sb) {
+                            b_slot -= (uint32_t)sb;
+                            ++b_pass;
+                        }
                     }
                 }
             } else {
                 // ---- MMA issuer ----
                 if (lane == 0) {
                     const uint32_t idesc = tc_idesc(n, BF16);
+                    const uint64_t bdesc0 = smem_desc(smem_addr(sB), 128, 512);
+                    uint32_t done = 0;
                     for (int e = 0; e < n_list && !stop; ++e) {
                         const uint32_t gi = base + (uint32_t)e;
-                        const uint32_t sa = gi & (sa_n - 1u), slot = gi % (uint32_t)sb;
+                        const uint32_t sa = gi & (sa_n - 1u), slot = b_slot;
                         if (!tc_wait(&fullA[sa], (gi >> sa_shift) & 1u, s_abort, A.err) ||
-                            !tc_wait(&fullB[slot], (gi / (uint32_t)sb) & 1u, s_abort, A.err)) {
+                            !tc_wait(&fullB[slot], b_pass & 1u, s_abort, A.err)) {
                             stop = true;
                             break;
                         }
+                        if (++b_slot == (uint32_t)sb) {
+                            b_slot = 0;
+                            ++b_pass;
+                        }
                         tc_fence_after();
                         const uint32_t a_col = tmem + (uint32_t)n + TC_ACOLS * sa;
-                        const uint32_t b_addr = smem_addr(sB + (size_t)slot * stage_bytes);
-                        mma_ts(tmem, a_col, smem_desc(b_addr, 128, 512), idesc, gi > 0 ? 1u : 0u);
-                        mma_ts(tmem, a_col + 8, smem_desc(b_addr + 256, 128, 512), idesc, 1u);
+                        const uint64_t bdesc = bdesc0 + (uint64_t)((slot * stage_bytes) >> 4);
+                        mma_ts(tmem, a_col, bdesc, idesc, gi > 0 ? 1u : 0u);
+                        mma_ts(tmem, a_col + 8, bdesc + (256 >> 4), idesc, 1u);
                         mma_commit(&emptyA[sa]);
                         mma_commit(&emptyB[slot]);
-                        misc[MW_ISSUED] = gi + 1u;
+                        done = gi + 1u;
                     }
+                    if (done) misc[MW_ISSUED] = done;
                 }
             }
             base += (uint32_t)n_list;
@@ -661,15 +679,16 @@ __global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_co
             }
         }
         tc_fence_before();
-    } else if (warp == NB / 32 && lane == 0 && *s_abort != 0u) {
-        // copies still in flight land before the CTA leaves: wait for the
-        // last use of every stage (bounded by time)
-        const uint32_t last = tma_issued;
-        const uint32_t first = last > (uint32_t)sb ? last - (uint32_t)sb : 0u;
+    } else if (warp == NB / 32 && lane < TC_PRODUCERS && *s_abort != 0u && tma_issued > 0) {
+        // copies this lane still has in flight land before the CTA leaves:
+        // wait for its last uses of the ring (bounded by time)
         const uint64_t t0 = global_ns();
-        for (uint32_t i = first; i < last; ++i) {
+        uint32_t i = tma_issued - 1u;
+        for (int c = 0; c < sb / TC_PRODUCERS; ++c) {
             while (!mbar_try_wait(&fullB[i % (uint32_t)sb], (i / (uint32_t)sb) & 1u))
                 if (global_ns() - t0 > TC_WAIT_NS) break;
+            if (i < (uint32_t)TC_PRODUCERS) break;
+            i -= TC_PRODUCERS;
         }
     }
     __syncthreads();
@@ -821,7 +840,8 @@ cudaError_t launch_tc(const TcArgs &args, int bf16, const void *z, int nch, int 
     const size_t stage = (size_t)64 * A.n;
     int sbv = fixed < budget ? (int)((budget - fixed) / stage) : 0;
     if (sbv > TC_MAX_SB) sbv = TC_MAX_SB;
-    if (sbv < 2) return cudaErrorInvalidConfiguration;
+    sbv -= sbv % TC_PRODUCERS;
+    if (sbv < TC_PRODUCERS) return cudaErrorInvalidConfiguration;
     A.sb = sbv;
     const size_t smem = tc_smem_layout(sbv, A.n, A.Q, has_w, eb, A.list_cap).total;
 
