@@ -237,3 +237,50 @@ def test_host_empty_large_block_round_trip(das):
     back = das.host_empty((n,), torch.uint8)
     back.copy_(d)
     assert torch.equal(back[:: 1 << 20], h[:: 1 << 20])
+
+
+DEGENERATE = {
+    # one voxel, one element, one transmit, the smallest K
+    "single": dict(n=(1, 1, 1), elems=(1, 1), n_tx=1, K=2, f_number=0.0),
+    "single_k64": dict(n=(1, 1, 1), elems=(1, 1), n_tx=1, K=64, f_number=0.0),
+    # a thin line of voxels and a line array, full aperture
+    "line": dict(n=(17, 1, 1), elems=(7, 1), n_tx=1, K=64, f_number=0.0),
+}
+
+
+@pytest.mark.parametrize("tc", [False, True])
+@pytest.mark.parametrize("name", sorted(DEGENERATE))
+def test_degenerate_shapes(das, oracle, name, tc):
+    """1 voxel / 1 element / 1 transmit, K = 2 (no term lies in range), thin
+    grids: CUDA-core and tensor-core paths against the oracle."""
+    sc = S.scene_tiny(iq=True, **DEGENERATE[name])
+    y = S.random_channels(sc, 3, seed=31)
+    plan = das.Plan.from_scene(sc, storage="f16" if tc else "f32", max_batch=3)
+    if tc:
+        plan.set_tuning(tensor_cores=True)
+    x = plan.forward(y.cuda()).cpu().numpy().reshape(3, -1)
+    plan.check()
+    plan.close()
+    ref = oracle.forward(sc, y.numpy())
+    if np.linalg.norm(ref) == 0.0:
+        assert np.count_nonzero(x) == 0
+    else:
+        assert rel_l2(x, ref) <= (2e-3 if tc else TOL_F32)
+
+
+@pytest.mark.parametrize("tc", [False, True])
+def test_no_voxel_inside_any_aperture(das, oracle, tc):
+    """Voxels at the depth of the array (z = 0 plane), f-number 1: every term
+    is outside the aperture and the image is exactly zero."""
+    sc = S.scene_tiny(iq=True, n=(9, 5, 3), elems=(3, 3), n_tx=2, K=64, f_number=1.0)
+    sc = sc.with_(origin=(sc.origin[0], sc.origin[1], -0.5e-3))
+    y = S.random_channels(sc, 2, seed=32)
+    ref = oracle.forward(sc, y.numpy())
+    assert np.count_nonzero(ref) == 0
+    plan = das.Plan.from_scene(sc, storage="f16" if tc else "f32", max_batch=2)
+    if tc:
+        plan.set_tuning(tensor_cores=True)
+    x = plan.forward(y.cuda()).cpu().numpy()
+    plan.check()
+    plan.close()
+    assert np.count_nonzero(x) == 0
