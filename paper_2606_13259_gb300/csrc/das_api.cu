@@ -327,6 +327,7 @@ int forward_tc(das_plan *p, const void *y, void *x, int B, cudaStream_t s) {
         return fail(DAS_ERR_INVALID_ARG, "tensor-core scratch holds %zu bytes, batch needs %zu", p->z_tc_bytes, need);
     const bool bf16 = p->storage == DAS_STORE_BF16;
     DAS_CU(launch_scale(y, p->scale, p->inv_scale, 1, p->storage, B, QM, p->K, s));
+    // the samples' factors go to inv_scale (scratch of the CUDA-core path, refilled there on every call)
     DAS_CU(launch_tc_stage(y, p->z_tc, p->rot, p->scale, p->inv_scale, p->ratio, p->smax, bf16 ? 1 : 0, B, bc, nch, n,
                            QM, p->K, s));
     p->launches += 3;

@@ -703,9 +703,13 @@ __global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_co
 // staging: scale ratios and the operand layout of the channel data
 // ---------------------------------------------------------------------------
 
-// ratio[qm] = scale[qm] / max(scale); *smax = max(scale).  One block.
+// Splits each (q, m) scale s between the two 16-bit operands: the samples are
+// stored times zinv = 1 / sqrt(s smax) (at most sqrt(s / smax) <= 1 in
+// magnitude) and the weights carry ratio = sqrt(s / smax), so neither operand
+// falls into the f16 subnormal range for quiet channels; ratio * zinv =
+// 1 / smax, and *smax = max(s) rescales the accumulator.  One block.
 __global__ void __launch_bounds__(1024) tc_ratio_kernel(const float *__restrict__ scale, float *__restrict__ ratio,
-                                                        float *__restrict__ smax, int QM) {
+                                                        float *__restrict__ zinv, float *__restrict__ smax, int QM) {
     __shared__ float red[32];
     float mx = 0.f;
     for (int i = threadIdx.x; i < QM; i += blockDim.x) mx = fmaxf(mx, scale[i]);
@@ -714,7 +718,10 @@ __global__ void __launch_bounds__(1024) tc_ratio_kernel(const float *__restrict_
     __syncthreads();
     mx = 0.f;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmaxf(mx, red[w]);
-    for (int i = threadIdx.x; i < QM; i += blockDim.x) ratio[i] = scale[i] / mx;
+    for (int i = threadIdx.x; i < QM; i += blockDim.x) {
+        ratio[i] = sqrtf(scale[i] / mx);
+        zinv[i] = 1.f / sqrtf(scale[i] * mx);
+    }
     if (threadIdx.x == 0) *smax = mx;
 }
 
@@ -723,7 +730,7 @@ __global__ void __launch_bounds__(1024) tc_ratio_kernel(const float *__restrict_
 template <bool BF16>
 __global__ void __launch_bounds__(128) tc_relayout_kernel(const float2 *__restrict__ y, uint4 *__restrict__ z,
                                                           const float2 *__restrict__ rot,
-                                                          const float *__restrict__ inv_scale, int B, int bc, int n,
+                                                          const float *__restrict__ zinv, int B, int bc, int n,
                                                           int QM, int K) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int c = blockIdx.z;
@@ -731,7 +738,7 @@ __global__ void __launch_bounds__(128) tc_relayout_kernel(const float2 *__restri
     const float2 r = rot ? rot[k] : make_float2(1.f, 0.f);
     const int nh = n >> 3;
     for (int qm = blockIdx.y; qm < QM; qm += gridDim.y) {
-        const float s = inv_scale[qm];
+        const float s = zinv[qm];
         for (int h = 0; h < nh; ++h) {
             uint32_t p[4], q[4];
 #pragma unroll
@@ -767,17 +774,17 @@ void tc_shape(int B, int &bc, int &nch, int &n) {
     n = ((2 * bc + 15) / 16) * 16;
 }
 
-cudaError_t launch_tc_stage(const void *y, void *z, const float2 *rot, const float *scale, const float *inv_scale,
+cudaError_t launch_tc_stage(const void *y, void *z, const float2 *rot, const float *scale, float *zinv,
                             float *ratio, float *smax, int bf16, int B, int bc, int nch, int n, int QM, int K,
                             cudaStream_t s) {
-    tc_ratio_kernel<<<1, 1024, 0, s>>>(scale, ratio, smax, QM);
+    tc_ratio_kernel<<<1, 1024, 0, s>>>(scale, ratio, zinv, smax, QM);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     dim3 grid((K + 127) / 128, QM < 65535 ? QM : 65535, nch);
     if (bf16)
-        tc_relayout_kernel<true><<<grid, 128, 0, s>>>((const float2 *)y, (uint4 *)z, rot, inv_scale, B, bc, n, QM, K);
+        tc_relayout_kernel<true><<<grid, 128, 0, s>>>((const float2 *)y, (uint4 *)z, rot, zinv, B, bc, n, QM, K);
     else
-        tc_relayout_kernel<false><<<grid, 128, 0, s>>>((const float2 *)y, (uint4 *)z, rot, inv_scale, B, bc, n, QM, K);
+        tc_relayout_kernel<false><<<grid, 128, 0, s>>>((const float2 *)y, (uint4 *)z, rot, zinv, B, bc, n, QM, K);
     return cudaGetLastError();
 }
 

@@ -30,7 +30,7 @@ struct TcArgs {
     const float *tx_tmin;
     const float *tx_tmax;
     const float *w_tx;
-    const float *ratio;   // [Q][M] storage scale divided by the largest one
+    const float *ratio;   // [Q][M] weight factor sqrt(scale / largest scale)
     const float *smax;    // the largest storage scale
     int *err;             // bit 2: a wait timed out; bit 3: an item needed more windows than a list holds
     unsigned long long *items;  // running count of MMA sub-items (128 x n x 32 each)
@@ -39,8 +39,8 @@ struct TcArgs {
 
 // Tensor-core path: channel data y[b][qm][k] (complex64) -> operand layout
 // z[c][qm][n/8][2][K][8] of 16-bit values (see das_tc.cu), the per-(q, m)
-// scale ratios and the largest scale.
-cudaError_t launch_tc_stage(const void *y, void *z, const float2 *rot, const float *scale, const float *inv_scale,
+// weight factors, the samples' factors (zinv) and the largest scale.
+cudaError_t launch_tc_stage(const void *y, void *z, const float2 *rot, const float *scale, float *zinv,
                             float *ratio, float *smax, int bf16, int B, int bc, int nch, int n, int QM, int K,
                             cudaStream_t s);
 cudaError_t launch_tc(const TcArgs &args, int bf16, const void *z, int nch, int ctas_per_sm, cudaStream_t s);
