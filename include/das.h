@@ -138,6 +138,12 @@ typedef struct {
                               DAS_STORE_BF16 only; the weights are rounded to the storage
                               type); 0: CUDA-core kernels (default).  Enabling it reserves
                               the operand scratch (2 x 2 bytes per sample and frame column). */
+    int tc_chain;          /* tensor-core path: largest number of MMA sub-items summed in one
+                              tensor-memory accumulation chain; at the first work-list end past it
+                              the chain is added into the image in float32 and the next one starts
+                              from zero, which keeps the tensor core's accumulation rounding
+                              bias proportional to the chain rather than to all terms
+                              (0: automatic, 1024; -1: one chain per tile) */
 } das_tuning_t;
 
 /* Build a plan (Sec. 2 problem statement: grid, receivers, observations, c).

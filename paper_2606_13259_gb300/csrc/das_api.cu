@@ -357,6 +357,7 @@ int forward_tc(das_plan *p, const void *y, void *x, int B, cudaStream_t s) {
     A.err = p->err;
     A.items = p->tc_items;
     A.x = reinterpret_cast<float2 *>(x);
+    A.chain = p->tuning.tc_chain == 0 ? TC_CHAIN_DEFAULT : (p->tuning.tc_chain < 0 ? 0 : p->tuning.tc_chain);
     p->tc_n = n;
     const bool timed = p->ev_used < (int)p->ev_start.size();
     if (timed) DAS_CU(cudaEventRecord(p->ev_start[p->ev_used], s));
@@ -685,7 +686,8 @@ int das_plan_timing(das_plan_t *plan, double *ms_total, int *launches) {
 
 int das_plan_set_tuning(das_plan_t *plan, const das_tuning_t *tuning) {
     if (!plan || !tuning) return fail(DAS_ERR_INVALID_ARG, "NULL argument");
-    if (tuning->frames_per_thread < 0 || tuning->ctas_per_sm < 0 || tuning->staging < 0 || tuning->tensor_cores < 0)
+    if (tuning->frames_per_thread < 0 || tuning->ctas_per_sm < 0 || tuning->staging < 0 || tuning->tensor_cores < 0 ||
+        tuning->tc_chain < -1)
         return fail(DAS_ERR_INVALID_ARG, "negative tuning value");
     if (tuning->tensor_cores && !tc_capable(plan))
         return fail(DAS_ERR_UNSUPPORTED, "the tensor-core path takes IQ data stored as f16 or bf16");

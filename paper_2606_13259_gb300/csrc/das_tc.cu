@@ -20,7 +20,12 @@
 //
 // one MMA of M = 128, N = 2 bc (padded to a multiple of 16, at most 256) and
 // K = 2 U = 32 (two K = 16 steps of kind::f16), accumulated in float32 in
-// TMEM over all items of the tile.
+// TMEM.  The tensor core's float32 accumulation loses a little of the running
+// sum at every step (measured as a gain deficit that grows in proportion to
+// the number of steps), so the items of a tile are summed in chains of a
+// bounded number of sub-items: at the end of a chain the builder threads add
+// D into the image with ordinary float32 arithmetic and the next chain starts
+// from zero.
 //
 // Window of an item.  With f = rf + t + delta (das_internal.cuh), t between
 // the tile's smallest and largest transmit rest (prepare kernel) and delta =
@@ -36,7 +41,7 @@
 // Operand layouts.
 //   A (W): TMEM, lanes = voxels (tile lane order), 16 columns of 32 bits per
 //          stage = 32 16-bit values, K-major: columns 0-7 Wr (u = 0..15),
-//          8-15 Wi.  Four stages.
+//          8-15 Wi.  A ring of sa stages (2 .. 16).
 //   B (window): shared memory, MN-major without swizzle.  The relayout
 //          stores the channel data as z[c][q m][n / 8][plane][k][8] 16-bit
 //          values, plane 0 = [Zr | Zi] and plane 1 = [-Zi | Zr] along n, so
@@ -46,14 +51,16 @@
 //          0 .. K-1 arrive as zeros.
 //   D: TMEM columns 0 .. n-1, lanes = voxels.
 //
-// CTA roles (192 threads): warps 0-3 build W (thread = voxel = TMEM lane) and
-// run the epilogue; warp 4 lane 0 issues the window copies; warp 5 lane 0
-// issues the MMAs and their commits.  Stages are handed over with mbarriers:
-// fullA (128 builder arrivals), fullB (TMA transaction bytes), emptyA /
-// emptyB (tcgen05.commit of the MMAs that read the stage), accFull (commit
-// after the last MMA).  Every wait is bounded; on expiry the CTA sets bit 2
-// of the plan's error word, drains what it has in flight and leaves without
-// writing its image tile.
+// CTA roles (G 128-thread builder groups + 2 warps): the builder threads
+// compute the work list and build W (thread = voxel = TMEM lane, group g
+// takes the sub-items with index = g mod G) and store D; lanes 0-3 of the
+// next warp issue the window copies; lane 0 of the last warp issues the MMAs
+// and their commits.  Stages are handed over with mbarriers: fullA (one
+// arrival per builder warp of a group), fullB (TMA transaction bytes),
+// emptyA / emptyB (tcgen05.commit of the MMAs that read the stage), accFull
+// (commit after the last MMA of a chain).  Every wait is bounded; on expiry
+// the CTA sets bit 2 of the plan's error word, drains what it has in flight
+// and leaves without writing its image tile.
 #include "das_async.cuh"
 #include "das_tc.cuh"
 
@@ -275,6 +282,59 @@ __host__ __device__ inline TcSmem tc_smem_layout(int sb, int n, int Q, bool has_
 enum : int { MW_TMEM = 0, MW_ABORT = 1, MW_ISSUED = 2, MW_NEL = 3, MW_NLIST = 4, MW_NEXT = 5, MW_CNT = 8,
              MW_SCAN = 40 };  // MW_CNT, MW_SCAN: one word per builder warp (up to 32)
 
+// D of a finished accumulation chain -> image, by the builder threads (whole
+// warps).  Waits for the chain's MMAs (accFull phase `parity`; bounded by time
+// only, since MMAs in flight must land before tensor memory is read or
+// reused), then each thread moves its voxel's frames b_first, b_first + 1, ...
+// in 16-frame blocks b_step apart: x = D smax, or x += D smax when x already
+// holds the earlier chains (add).  read_d false: no MMA ran, the frames get D = 0.
+__device__ __noinline__ void tc_store_d(const TcArgs &A, uint32_t taddr, uint64_t *accFull, uint32_t parity, bool add,
+                                        bool read_d, volatile uint32_t *s_abort, int lane, int b_first, int b_step,
+                                        int chunk, bool valid, long long nvox) {
+    bool ok = true;
+    if (read_d && lane == 0) {
+        const uint64_t t0 = global_ns();
+        while (!(ok = mbar_try_wait(accFull, parity)))
+            if (global_ns() - t0 > TC_WAIT_NS) break;
+        if (!ok) {
+            atomicOr(A.err, 4);
+            *s_abort = 1u;
+        }
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0) != 0 && *s_abort == 0u;
+    __syncwarp();
+    tc_fence_after();
+    const float sm = *A.smax;
+    for (int b0 = b_first; b0 < A.bc; b0 += b_step) {
+        uint32_t re[16], im[16];
+        if (read_d) {
+            tmem_ld16(taddr + (uint32_t)b0, re);
+            tmem_ld16(taddr + (uint32_t)(A.bc + b0), im);
+            tmem_ld_wait();
+        } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) re[i] = im[i] = 0u;
+        }
+        if (ok && valid) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int b = b0 + i;
+                const long long frame = (long long)chunk * A.bc + b;
+                if (b < A.bc && frame < A.B) {
+                    float2 *px = A.x + frame * A.g.n_voxels + nvox;
+                    float2 v = make_float2(__uint_as_float(re[i]) * sm, __uint_as_float(im[i]) * sm);
+                    if (add) {
+                        const float2 o = *px;
+                        v = make_float2(o.x + v.x, o.y + v.y);
+                    }
+                    *px = v;
+                }
+            }
+        }
+    }
+    tc_fence_before();
+}
+
 template <bool BF16, int G, int MINB>
 __global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_constant__ CUtensorMap zmap,
                                                                  const __grid_constant__ TcArgs A) {
@@ -362,7 +422,16 @@ __global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_co
     const float dz = (float)(g.sz * (lz - 0.5 * (TILE_Z - 1)));
     const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
 
+    // image rows of a builder thread: its voxel, its TMEM lane, its first 16-frame block
+    const long long nvox = ((long long)iz * g.ny + iy) * g.nx + ix;
+    const uint32_t lane_d = (uint32_t)((warp & 3) * 32) << 16;
+    const int b_first = 16 * (tid >> 7);
+
     uint32_t base = 0;  // sub-items of earlier rounds (same value in every thread)
+    // accumulation chains (same values in every thread): first sub-item of the
+    // current chain, commits to accFull so far, whether x already holds a sum
+    uint32_t chain0 = 0, n_commit = 0;
+    bool folded = false;
     const size_t qm_base = (size_t)chunk * Q * M;
     bool stop = misc[MW_ABORT] != 0u;
     uint32_t tma_issued = 0;  // producer: window copies issued
@@ -434,6 +503,15 @@ __global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_co
         const int P = n_el * Q;  // (element, transmit) pairs, element-major
 
         for (int p0 = 0; p0 < P;) {
+            // A chain that has reached its length ends here: its MMAs are
+            // committed now and the builders add D into the image once they
+            // have built this round's list, so that the last MMAs finish
+            // while the list is built (all threads take the same decision).
+            const uint32_t issued = misc[MW_ISSUED];  // written before the last barrier
+            const bool new_chain = A.chain > 0 && base - chain0 >= (uint32_t)A.chain;
+            const bool fold = new_chain && issued > chain0;
+            if (fold && warp == NB / 32 + 1 && lane == 0) mma_commit(accFull);
+
             // ---- sub-item list of pairs p0 .. (as many as fit), by the builder threads ----
             const int per = (P - p0 + NB - 1) / NB;
             const int pa = min(P, p0 + tid * per), pe = min(P, pa + per);
@@ -485,7 +563,16 @@ __global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_co
                     atomicMax(&misc[MW_NLIST], (uint32_t)off);
                 }
             }
-            __syncthreads();
+            if (fold && tid < NB)
+                tc_store_d(A, tmem + lane_d, accFull, n_commit & 1u, folded, true, s_abort, lane, b_first, 16 * G,
+                           chunk, valid, nvox);
+            if (fold) {
+                ++n_commit;
+                folded = true;
+            }
+            if (new_chain) chain0 = base;
+            __syncthreads();  // the list is complete and D of an ended chain has been read
+            tc_fence_after();
             const int n_list = (int)misc[MW_NLIST];
             const int p_next = (int)misc[MW_NEXT];
 
@@ -618,7 +705,7 @@ __global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_co
                         tc_fence_after();
                         const uint32_t a_col = tmem + (uint32_t)n + TC_ACOLS * sa;
                         const uint64_t bdesc = bdesc0 + (uint64_t)((slot * stage_bytes) >> 4);
-                        mma_ts(tmem, a_col, bdesc, idesc, gi > 0 ? 1u : 0u);
+                        mma_ts(tmem, a_col, bdesc, idesc, gi != chain0 ? 1u : 0u);
                         mma_ts(tmem, a_col + 8, bdesc + (256 >> 4), idesc, 1u);
                         mma_commit(&emptyA[sa]);
                         mma_commit(&emptyB[slot]);
@@ -635,50 +722,16 @@ __global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_co
     }
 
     const uint32_t issued = misc[MW_ISSUED];  // written by the MMA thread before the last barrier
-    if (warp == NB / 32 + 1 && lane == 0 && issued > 0) {
-        mma_commit(accFull);
-        atomicAdd(A.items, (unsigned long long)issued);
+    if (warp == NB / 32 + 1 && lane == 0) {
+        if (issued > chain0) mma_commit(accFull);
+        if (issued > 0) atomicAdd(A.items, (unsigned long long)issued);
     }
 
     if (tid < NB) {
-        // ---- epilogue: D (TMEM) -> image; the groups take alternate 16-frame blocks ----
-        // MMAs still in flight must land before the tensor memory is read or
-        // released, so this wait ignores aborts and is bounded by time only.
-        bool ok = true;
-        if (issued > 0 && lane == 0) {
-            const uint64_t t0 = global_ns();
-            while (!(ok = mbar_try_wait(accFull, 0u)))
-                if (global_ns() - t0 > TC_WAIT_NS) break;
-            if (!ok) atomicOr(A.err, 4);
-        }
-        ok = __shfl_sync(0xffffffffu, ok, 0) != 0 && *s_abort == 0u;
-        __syncwarp();
-        tc_fence_after();
-        const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
-        const float sm = *A.smax;
-        const long long nvox = ((long long)iz * g.ny + iy) * g.nx + ix;
-        for (int b0 = 16 * (tid >> 7); b0 < A.bc; b0 += 16 * G) {
-            uint32_t re[16], im[16];
-            if (issued > 0) {
-                tmem_ld16(tmem + lane_base + (uint32_t)b0, re);
-                tmem_ld16(tmem + lane_base + (uint32_t)(A.bc + b0), im);
-                tmem_ld_wait();
-            } else {
-#pragma unroll
-                for (int i = 0; i < 16; ++i) re[i] = im[i] = 0u;
-            }
-            if (ok && valid) {
-#pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int b = b0 + i;
-                    const long long frame = (long long)chunk * A.bc + b;
-                    if (b < A.bc && frame < A.B)
-                        A.x[frame * g.n_voxels + nvox] =
-                            make_float2(__uint_as_float(re[i]) * sm, __uint_as_float(im[i]) * sm);
-                }
-            }
-        }
-        tc_fence_before();
+        // ---- epilogue: the last chain's D (TMEM) -> image ----
+        if (issued > chain0 || !folded)
+            tc_store_d(A, tmem + lane_d, accFull, n_commit & 1u, folded, issued > chain0, s_abort, lane, b_first,
+                       16 * G, chunk, valid, nvox);
     } else if (warp == NB / 32 && lane < TC_PRODUCERS && *s_abort != 0u && tma_issued > 0) {
         // copies this lane still has in flight land before the CTA leaves:
         // wait for its last uses of the ring (bounded by time)
@@ -841,6 +894,8 @@ cudaError_t launch_tc(const TcArgs &args, int bf16, const void *z, int nch, int 
     long long cap = (long long)eb * A.Q;
     if (cap < 256) cap = 256;
     if (cap > TC_LIST_MAX) cap = TC_LIST_MAX;
+    // a chain ends at a list end: lists no longer than a chain keep chains short
+    if (A.chain > 0 && cap > A.chain) cap = A.chain < 256 ? 256 : A.chain;
     A.list_cap = (int)cap;
     const size_t budget = (size_t)(227 * 1024) / per_sm - 1024;  // per-CTA share incl. the runtime's reserve
     const size_t fixed = tc_smem_layout(0, A.n, A.Q, has_w, eb, A.list_cap).total;

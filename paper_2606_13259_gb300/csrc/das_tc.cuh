@@ -6,6 +6,9 @@
 
 namespace das {
 
+// Sub-items of one tensor-memory accumulation chain unless the tuning sets it.
+constexpr int TC_CHAIN_DEFAULT = 1024;
+
 // Arguments of the tensor-core forward kernel (das_tc.cu).
 struct TcArgs {
     GridDesc g;
@@ -16,6 +19,7 @@ struct TcArgs {
     int sb;           // window stages in shared memory
     int sa;           // weight stages in tensor memory (power of two)
     int list_cap;     // sub-items per work list
+    int chain;        // sub-items per accumulation chain before D is added into x (0: one chain)
     int ncols;        // tensor-memory columns the CTA allocates
     float a;          // fs / c
     double ad;

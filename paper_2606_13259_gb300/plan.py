@@ -123,11 +123,13 @@ class Plan:
         return {f: getattr(i, f) for f, _ in L.PlanInfo._fields_}
 
     def set_tuning(self, frames_per_thread: int = 0, ctas_per_sm: int = 0, staging: bool = False,
-                   load_width: int = 0, tensor_cores: bool = False) -> None:
+                   load_width: int = 0, tensor_cores: bool = False, tc_chain: int = 0) -> None:
         """Kernel shape of the forward pass; tensor_cores selects the tcgen05
-        contraction (IQ data with f16 / bf16 storage)."""
+        contraction (IQ data with f16 / bf16 storage), tc_chain the MMA
+        sub-items per tensor-memory accumulation chain (0: automatic, -1: one
+        chain per tile)."""
         t = L.Tuning(int(frames_per_thread), int(ctas_per_sm), 1 if staging else 0, int(load_width),
-                     1 if tensor_cores else 0)
+                     1 if tensor_cores else 0, int(tc_chain))
         L.check(self._lib.das_plan_set_tuning(self._h, C.byref(t)))
 
     def check(self, stream=None) -> None:
@@ -308,7 +310,7 @@ class Batch:
             pass
 
     def set_tuning(self, frames_per_thread: int = 0, ctas_per_sm: int = 0, staging: bool = False) -> None:
-        t = L.Tuning(int(frames_per_thread), int(ctas_per_sm), 1 if staging else 0, 0, 0)
+        t = L.Tuning(int(frames_per_thread), int(ctas_per_sm), 1 if staging else 0, 0, 0, 0)
         L.check(self._lib.das_batch_set_tuning(self._h, C.byref(t)))
 
     def info(self) -> dict:

@@ -30,9 +30,9 @@ def das():
     return P
 
 
-def tc_forward(das, scene, y, storage="f16", ctas_per_sm=0):
+def tc_forward(das, scene, y, storage="f16", ctas_per_sm=0, tc_chain=0):
     plan = das.Plan.from_scene(scene, storage=storage, max_batch=y.shape[0])
-    plan.set_tuning(tensor_cores=True, ctas_per_sm=ctas_per_sm)
+    plan.set_tuning(tensor_cores=True, ctas_per_sm=ctas_per_sm, tc_chain=tc_chain)
     x = plan.forward(y if y.is_cuda else y.cuda())
     plan.check()
     plan.close()
@@ -67,6 +67,18 @@ def test_mma_widths_and_frame_chunks(das, oracle, B):
     y = S.random_channels(sc, B, seed=B)
     x = tc_forward(das, sc, y).cpu().numpy()
     assert rel_l2(x, oracle.forward(sc, y.numpy())) <= TOL["f16"]
+
+
+@pytest.mark.parametrize("chain,ctas,B", [(-1, 0, 3), (1, 0, 3), (1, 1, 3), (300, 0, 3), (1, 0, 130)])
+def test_accumulation_chains(das, oracle, chain, ctas, B):
+    """D added into the image at every list end (chain 1), after a few lists
+    (300), or once per tile (-1); two and four builder groups; two frame chunks."""
+    sc = S.scene_small_iq()
+    y = S.frames(sc, B, seed=1, n_speckle=2000, points=S.SMALL_POINTS, noise_db=30.0)
+    x = tc_forward(das, sc, y, ctas_per_sm=ctas, tc_chain=chain).cpu().numpy()
+    err = rel_l2(x, oracle.forward(sc, y.numpy()))
+    print(f"chain {chain}, ctas/SM {ctas or 'auto'}, {B} frames: relative L2 {err:.3e}")
+    assert err <= TOL["f16"]
 
 
 def test_transmit_weights_and_one_cta_per_sm(das, oracle):
@@ -111,6 +123,25 @@ def test_paper_scale_sampled(das, oracle):
     err = rel_l2(got, oracle.forward(sc, y.cpu().numpy(), voxels=vox))
     print(f"paper scale, tensor cores: relative L2 {err:.3e}")
     assert err <= TOL["f16"]
+
+
+def test_paper_scale_gain_at_point_targets(das, oracle):
+    """The tensor core's float32 accumulation loses a little of the running
+    sum at every step, a gain deficit proportional to the chain length (about
+    7e-4 at the point targets of the paper workload with one chain per tile).
+    With the default chains of 1024 sub-items the gain at the ten point
+    targets stays within 1.5e-4 of the oracle's."""
+    sc = S.scene_paper()
+    B = 20
+    y = S.frames(sc, B, seed=2, n_speckle=20000, points=S.paper_points(sc), device="cuda")
+    pts = np.array([sc.voxel_index(*p) for p in S.paper_points(sc)])
+    ref = oracle.forward(sc, y.cpu().numpy(), voxels=pts)
+    gains = {}
+    for chain in (0, -1):
+        got = tc_forward(das, sc, y, tc_chain=chain)[:, torch.as_tensor(pts, device="cuda")].cpu().numpy()
+        gains[chain] = float(np.real(np.vdot(ref, got)) / np.vdot(ref, ref).real) - 1.0
+    print(f"gain error at the point targets: chains of 1024 {gains[0]:+.2e}, one chain {gains[-1]:+.2e}")
+    assert abs(gains[0]) <= 1.5e-4
 
 
 def test_table1_configuration_sampled(das, oracle):
