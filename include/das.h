@@ -143,7 +143,8 @@ typedef struct {
                               the chain is added into the image in float32 and the next one starts
                               from zero, which keeps the tensor core's accumulation rounding
                               bias proportional to the chain rather than to all terms
-                              (0: automatic, 1024; -1: one chain per tile) */
+                              (0: automatic, 1024 for plans of 4 or more transmits and one
+                              chain per tile otherwise; -1: one chain per tile) */
 } das_tuning_t;
 
 /* Build a plan (Sec. 2 problem statement: grid, receivers, observations, c).
@@ -181,6 +182,22 @@ int das_forward(das_plan_t *plan, const void *y_dev, void *x_dev, int batch, das
  * on `stream`.  Pinned host memory is needed for full speed; memory from
  * das_host_alloc keeps it after long kernels. */
 int das_forward_host(das_plan_t *plan, const void *y_host, void *x_host, int batch, das_stream_t stream);
+
+/* das_forward_host over a sequence of n_batches batches of `batch` frames
+ * each (no counterpart in the paper: host I/O around Eq. 2), with the copies
+ * overlapped with the forward passes.  y_host[i] ([batch][Q][M][K] of
+ * sample_type) and x_host[i] ([batch][N] image) are the host buffers of
+ * batch i; the same input buffer may appear several times, an output buffer
+ * may appear once only.  While the forward pass of batch i runs on `stream`,
+ * the inputs of batch i + 1 are copied into a second device staging slot and
+ * the image of batch i - 1 is copied out, each split into up to 16 pieces on
+ * the plan's copy streams.  Returns when every image is in host memory.  The
+ * first call allocates two staging slots (inputs and images for max_batch
+ * frames each) and the copy events.  Every (y_host[i], x_host[i]) pair is
+ * checked before any copy; NULL arrays or n_batches < 1 give
+ * DAS_ERR_INVALID_ARG. */
+int das_forward_host_many(das_plan_t *plan, const void *const *y_host, void *const *x_host, int n_batches,
+                          int batch, das_stream_t stream);
 
 /* Page-locked host memory for the host calls (no counterpart in the paper):
  * `bytes` rounded up to whole transparent huge pages, advised as huge pages,

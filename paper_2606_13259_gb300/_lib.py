@@ -24,7 +24,7 @@ EXPORTS = ["das_plan_create", "das_plan_destroy", "das_plan_set_c", "das_plan_in
            "das_forward", "das_forward_host", "das_adjoint", "das_grad_c", "das_count_active",
            "das_plan_enable_timing", "das_plan_timing", "das_last_error", "das_version", "das_grad_c_static",
            "das_plan_check", "das_batch_create", "das_batch_forward", "das_batch_set_tuning", "das_batch_info",
-           "das_batch_destroy", "das_host_alloc", "das_host_free"]
+           "das_batch_destroy", "das_host_alloc", "das_host_free", "das_forward_host_many"]
 
 
 class Geometry(C.Structure):
@@ -89,6 +89,8 @@ def lib():
         for name in ("das_forward", "das_forward_host", "das_adjoint"):
             getattr(L, name).argtypes = [vp, vp, vp, i, vp]
             getattr(L, name).restype = i
+        L.das_forward_host_many.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), i, i, vp]
+        L.das_forward_host_many.restype = i
         L.das_grad_c.argtypes = [vp, vp, vp, vp, i, vp]
         L.das_grad_c.restype = i
         L.das_grad_c_static.argtypes = [vp, vp, vp, vp, i, vp]

@@ -77,10 +77,14 @@ struct das_plan {
     double *partial = nullptr;
     size_t partial_n = 0;
     double *scalar = nullptr;
-    void *stage_y = nullptr;
-    void *stage_x = nullptr;
+    void *stage_y[2] = {nullptr, nullptr};  // host calls: device staging of inputs / images
+    void *stage_x[2] = {nullptr, nullptr};  //   (slot 1 only for the overlapped sequence call)
     std::vector<cudaStream_t> copy_streams;  // host calls: copies split across these
     std::vector<cudaEvent_t> copy_events;    // [0] start, [1 + i] end of stream i
+    // overlapped sequence call, per staging slot: ends of the input pieces,
+    // ends of the image pieces, end of the forward pass
+    std::vector<cudaEvent_t> in_done[2], out_done[2];
+    cudaEvent_t fwd_done[2] = {nullptr, nullptr};
     void *z_tc = nullptr;      // tensor-core operand layout of the channel data
     size_t z_tc_bytes = 0;
     float *ratio = nullptr;    // [Q][M] scale / largest scale (tensor-core path)
@@ -357,7 +361,8 @@ int forward_tc(das_plan *p, const void *y, void *x, int B, cudaStream_t s) {
     A.err = p->err;
     A.items = p->tc_items;
     A.x = reinterpret_cast<float2 *>(x);
-    A.chain = p->tuning.tc_chain == 0 ? TC_CHAIN_DEFAULT : (p->tuning.tc_chain < 0 ? 0 : p->tuning.tc_chain);
+    A.chain = p->tuning.tc_chain > 0 ? p->tuning.tc_chain
+              : (p->tuning.tc_chain == 0 && p->Q >= TC_CHAIN_MIN_TX ? TC_CHAIN_DEFAULT : 0);
     p->tc_n = n;
     const bool timed = p->ev_used < (int)p->ev_start.size();
     if (timed) DAS_CU(cudaEventRecord(p->ev_start[p->ev_used], s));
@@ -600,6 +605,11 @@ void das_plan_destroy(das_plan_t *plan) {
     destroy_events(plan);
     for (cudaStream_t cs : plan->copy_streams) cudaStreamDestroy(cs);
     for (cudaEvent_t ce : plan->copy_events) cudaEventDestroy(ce);
+    for (int j = 0; j < 2; ++j) {
+        for (cudaEvent_t ce : plan->in_done[j]) cudaEventDestroy(ce);
+        for (cudaEvent_t ce : plan->out_done[j]) cudaEventDestroy(ce);
+        if (plan->fwd_done[j]) cudaEventDestroy(plan->fwd_done[j]);
+    }
     for (void *a : plan->allocs) cudaFree(a);
     delete plan;
 }
@@ -739,33 +749,127 @@ int das_forward(das_plan_t *plan, const void *y_dev, void *x_dev, int batch, das
     return DAS_OK;
 }
 
+// Staging slots 0 .. slots-1, copy streams and events of the host calls
+// (created on first use).
+static int ensure_host_io(das_plan *p, int slots) {
+    int rc;
+    const size_t ybytes = (size_t)p->max_batch * p->Q * p->M * p->K * sample_bytes_public(p);
+    const size_t xbytes = (size_t)p->max_batch * p->g.n_voxels * sample_bytes_public(p);
+    for (int j = 0; j < slots; ++j) {
+        if (!p->stage_y[j] && (rc = dalloc(p, &p->stage_y[j], ybytes, "host-call input staging")) != DAS_OK)
+            return rc;
+        if (!p->stage_x[j] && (rc = dalloc(p, &p->stage_x[j], xbytes, "host-call output staging")) != DAS_OK)
+            return rc;
+    }
+    if (p->copy_streams.empty()) {
+        for (int i = 0; i < HOST_COPY_STREAMS; ++i) {
+            cudaStream_t cs;
+            DAS_CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+            p->copy_streams.push_back(cs);
+        }
+        for (int i = 0; i <= HOST_COPY_STREAMS; ++i) {
+            cudaEvent_t ce;
+            DAS_CU(cudaEventCreateWithFlags(&ce, cudaEventDisableTiming));
+            p->copy_events.push_back(ce);
+        }
+    }
+    if (slots > 1 && !p->fwd_done[0]) {
+        for (int j = 0; j < 2; ++j) {
+            for (int i = 0; i < HOST_COPY_STREAMS; ++i) {
+                cudaEvent_t a, b;
+                DAS_CU(cudaEventCreateWithFlags(&a, cudaEventDisableTiming));
+                p->in_done[j].push_back(a);
+                DAS_CU(cudaEventCreateWithFlags(&b, cudaEventDisableTiming));
+                p->out_done[j].push_back(b);
+            }
+            DAS_CU(cudaEventCreateWithFlags(&p->fwd_done[j], cudaEventDisableTiming));
+        }
+    }
+    return DAS_OK;
+}
+
 int das_forward_host(das_plan_t *plan, const void *y_host, void *x_host, int batch, das_stream_t stream) {
     g_err[0] = 0;
     int rc = check_call(plan, y_host, x_host, batch);
     if (rc != DAS_OK) return rc;
     DeviceGuard guard(plan->device);
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t ybytes = (size_t)plan->max_batch * plan->Q * plan->M * plan->K * sample_bytes_public(plan);
-    const size_t xbytes = (size_t)plan->max_batch * plan->g.n_voxels * sample_bytes_public(plan);
-    if (!plan->stage_y && (rc = dalloc(plan, &plan->stage_y, ybytes, "host-call input staging")) != DAS_OK) return rc;
-    if (!plan->stage_x && (rc = dalloc(plan, &plan->stage_x, xbytes, "host-call output staging")) != DAS_OK) return rc;
-    if (plan->copy_streams.empty()) {
-        for (int i = 0; i < HOST_COPY_STREAMS; ++i) {
-            cudaStream_t cs;
-            DAS_CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-            plan->copy_streams.push_back(cs);
-        }
-        for (int i = 0; i <= HOST_COPY_STREAMS; ++i) {
-            cudaEvent_t ce;
-            DAS_CU(cudaEventCreateWithFlags(&ce, cudaEventDisableTiming));
-            plan->copy_events.push_back(ce);
-        }
-    }
+    if ((rc = ensure_host_io(plan, 1)) != DAS_OK) return rc;
     const size_t yb = (size_t)batch * plan->Q * plan->M * plan->K * sample_bytes_public(plan);
     const size_t xb = (size_t)batch * plan->g.n_voxels * sample_bytes_public(plan);
-    if ((rc = copy_split(plan, plan->stage_y, y_host, yb, cudaMemcpyHostToDevice, s)) != DAS_OK) return rc;
-    if ((rc = das_forward(plan, plan->stage_y, plan->stage_x, batch, stream)) != DAS_OK) return rc;
-    if ((rc = copy_split(plan, x_host, plan->stage_x, xb, cudaMemcpyDeviceToHost, s)) != DAS_OK) return rc;
+    if ((rc = copy_split(plan, plan->stage_y[0], y_host, yb, cudaMemcpyHostToDevice, s)) != DAS_OK) return rc;
+    if ((rc = das_forward(plan, plan->stage_y[0], plan->stage_x[0], batch, stream)) != DAS_OK) return rc;
+    if ((rc = copy_split(plan, x_host, plan->stage_x[0], xb, cudaMemcpyDeviceToHost, s)) != DAS_OK) return rc;
+    DAS_CU(cudaStreamSynchronize(s));
+    return DAS_OK;
+}
+
+// `bytes` as up to HOST_COPY_STREAMS pieces (at least 16 MB each) on the copy
+// streams, each after `after` (if any); piece i records done[i].  Returns
+// the number of pieces.
+static int copy_pieces(das_plan *p, void *dst, const void *src, size_t bytes, cudaMemcpyKind kind,
+                       cudaEvent_t after, const std::vector<cudaEvent_t> &done, int *pieces_out) {
+    const size_t min_piece = (size_t)16 << 20;
+    int pieces = (int)((bytes + min_piece - 1) / min_piece);
+    if (pieces > HOST_COPY_STREAMS) pieces = HOST_COPY_STREAMS;
+    if (pieces < 1) pieces = 1;
+    const size_t piece = ((bytes + pieces - 1) / pieces + 255) / 256 * 256;
+    int n = 0;
+    for (int i = 0; i < pieces; ++i) {
+        const size_t off = (size_t)i * piece;
+        if (off >= bytes && i > 0) break;
+        const size_t len = off + piece <= bytes ? piece : bytes - off;
+        cudaStream_t cs = p->copy_streams[i];
+        if (after) DAS_CU(cudaStreamWaitEvent(cs, after, 0));
+        if (len > 0) DAS_CU(cudaMemcpyAsync((char *)dst + off, (const char *)src + off, len, kind, cs));
+        DAS_CU(cudaEventRecord(done[i], cs));
+        ++n;
+    }
+    *pieces_out = n;
+    return DAS_OK;
+}
+
+int das_forward_host_many(das_plan_t *plan, const void *const *y_host, void *const *x_host, int n_batches,
+                          int batch, das_stream_t stream) {
+    g_err[0] = 0;
+    if (!plan || !y_host || !x_host) return fail(DAS_ERR_INVALID_ARG, "NULL argument");
+    if (n_batches < 1) return fail(DAS_ERR_INVALID_ARG, "n_batches must be >= 1");
+    int rc;
+    for (int i = 0; i < n_batches; ++i)
+        if ((rc = check_call(plan, y_host[i], x_host[i], batch)) != DAS_OK) return rc;
+    DeviceGuard guard(plan->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((rc = ensure_host_io(plan, 2)) != DAS_OK) return rc;
+    const size_t yb = (size_t)batch * plan->Q * plan->M * plan->K * sample_bytes_public(plan);
+    const size_t xb = (size_t)batch * plan->g.n_voxels * sample_bytes_public(plan);
+    int n_in[2] = {0, 0}, n_out[2] = {0, 0};
+    bool used[2] = {false, false};
+    // inputs of batch 0 (the copy streams first wait for the work already on `stream`)
+    DAS_CU(cudaEventRecord(plan->copy_events[0], s));
+    if ((rc = copy_pieces(plan, plan->stage_y[0], y_host[0], yb, cudaMemcpyHostToDevice, plan->copy_events[0],
+                          plan->in_done[0], &n_in[0])) != DAS_OK)
+        return rc;
+    for (int i = 0; i < n_batches; ++i) {
+        const int j = i & 1, jn = j ^ 1;
+        // inputs of batch i + 1 into the other slot once batch i - 1 has read it
+        if (i + 1 < n_batches &&
+            (rc = copy_pieces(plan, plan->stage_y[jn], y_host[i + 1], yb, cudaMemcpyHostToDevice,
+                              used[jn] ? plan->fwd_done[jn] : plan->copy_events[0], plan->in_done[jn], &n_in[jn])) !=
+                DAS_OK)
+            return rc;
+        // forward pass of batch i once its inputs are in and slot j's image of batch i - 2 is out
+        for (int k = 0; k < n_in[j]; ++k) DAS_CU(cudaStreamWaitEvent(s, plan->in_done[j][k], 0));
+        for (int k = 0; k < n_out[j]; ++k) DAS_CU(cudaStreamWaitEvent(s, plan->out_done[j][k], 0));
+        if ((rc = das_forward(plan, plan->stage_y[j], plan->stage_x[j], batch, stream)) != DAS_OK) return rc;
+        DAS_CU(cudaEventRecord(plan->fwd_done[j], s));
+        used[j] = true;
+        // image of batch i out while batch i + 1 runs
+        if ((rc = copy_pieces(plan, x_host[i], plan->stage_x[j], xb, cudaMemcpyDeviceToHost, plan->fwd_done[j],
+                              plan->out_done[j], &n_out[j])) != DAS_OK)
+            return rc;
+    }
+    for (int j = 0; j < 2; ++j)
+        for (int k = 0; k < n_out[j]; ++k) DAS_CU(cudaStreamWaitEvent(s, plan->out_done[j][k], 0));
     DAS_CU(cudaStreamSynchronize(s));
     return DAS_OK;
 }

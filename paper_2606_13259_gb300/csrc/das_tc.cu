@@ -335,7 +335,7 @@ __device__ __noinline__ void tc_store_d(const TcArgs &A, uint32_t taddr, uint64_
     tc_fence_before();
 }
 
-template <bool BF16, int G, int MINB>
+template <bool BF16, int G, int MINB, bool CHAIN>
 __global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_constant__ CUtensorMap zmap,
                                                                  const __grid_constant__ TcArgs A) {
     constexpr int NB = G * TILE_N;  // builder threads
@@ -507,8 +507,8 @@ __global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_co
             // committed now and the builders add D into the image once they
             // have built this round's list, so that the last MMAs finish
             // while the list is built (all threads take the same decision).
-            const uint32_t issued = misc[MW_ISSUED];  // written before the last barrier
-            const bool new_chain = A.chain > 0 && base - chain0 >= (uint32_t)A.chain;
+            const uint32_t issued = CHAIN ? misc[MW_ISSUED] : 0u;  // written before the last barrier
+            const bool new_chain = CHAIN && base - chain0 >= (uint32_t)A.chain;
             const bool fold = new_chain && issued > chain0;
             if (fold && warp == NB / 32 + 1 && lane == 0) mma_commit(accFull);
 
@@ -572,7 +572,7 @@ __global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_co
             }
             if (new_chain) chain0 = base;
             __syncthreads();  // the list is complete and D of an ended chain has been read
-            tc_fence_after();
+            if constexpr (CHAIN) tc_fence_after();
             const int n_list = (int)misc[MW_NLIST];
             const int p_next = (int)misc[MW_NEXT];
 
@@ -705,7 +705,8 @@ __global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_co
                         tc_fence_after();
                         const uint32_t a_col = tmem + (uint32_t)n + TC_ACOLS * sa;
                         const uint64_t bdesc = bdesc0 + (uint64_t)((slot * stage_bytes) >> 4);
-                        mma_ts(tmem, a_col, bdesc, idesc, gi != chain0 ? 1u : 0u);
+                        // the first sub-item of a chain starts from zero
+                        mma_ts(tmem, a_col, bdesc, idesc, (CHAIN ? gi != chain0 : gi > 0) ? 1u : 0u);
                         mma_ts(tmem, a_col + 8, bdesc + (256 >> 4), idesc, 1u);
                         mma_commit(&emptyA[sa]);
                         mma_commit(&emptyB[slot]);
@@ -729,9 +730,48 @@ __global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_co
 
     if (tid < NB) {
         // ---- epilogue: the last chain's D (TMEM) -> image ----
-        if (issued > chain0 || !folded)
-            tc_store_d(A, tmem + lane_d, accFull, n_commit & 1u, folded, issued > chain0, s_abort, lane, b_first,
-                       16 * G, chunk, valid, nvox);
+        if constexpr (CHAIN) {
+            if (issued > chain0 || !folded)
+                tc_store_d(A, tmem + lane_d, accFull, n_commit & 1u, folded, issued > chain0, s_abort, lane, b_first,
+                           16 * G, chunk, valid, nvox);
+        } else {
+            // one chain: x = D smax; the groups take alternate 16-frame blocks.
+            // MMAs still in flight must land before the tensor memory is read
+            // or released, so this wait ignores aborts and is bounded by time only.
+            bool ok = true;
+            if (issued > 0 && lane == 0) {
+                const uint64_t t0 = global_ns();
+                while (!(ok = mbar_try_wait(accFull, 0u)))
+                    if (global_ns() - t0 > TC_WAIT_NS) break;
+                if (!ok) atomicOr(A.err, 4);
+            }
+            ok = __shfl_sync(0xffffffffu, ok, 0) != 0 && *s_abort == 0u;
+            __syncwarp();
+            tc_fence_after();
+            const float sm = *A.smax;
+            for (int b0 = b_first; b0 < A.bc; b0 += 16 * G) {
+                uint32_t re[16], im[16];
+                if (issued > 0) {
+                    tmem_ld16(tmem + lane_d + (uint32_t)b0, re);
+                    tmem_ld16(tmem + lane_d + (uint32_t)(A.bc + b0), im);
+                    tmem_ld_wait();
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) re[i] = im[i] = 0u;
+                }
+                if (ok && valid) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const int b = b0 + i;
+                        const long long frame = (long long)chunk * A.bc + b;
+                        if (b < A.bc && frame < A.B)
+                            A.x[frame * g.n_voxels + nvox] =
+                                make_float2(__uint_as_float(re[i]) * sm, __uint_as_float(im[i]) * sm);
+                    }
+                }
+            }
+            tc_fence_before();
+        }
     } else if (warp == NB / 32 && lane < TC_PRODUCERS && *s_abort != 0u && tma_issued > 0) {
         // copies this lane still has in flight land before the CTA leaves:
         // wait for its last uses of the ring (bounded by time)
@@ -863,7 +903,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 
 template <bool BF16, int G, int MINB>
 static cudaError_t launch_tc_t(const CUtensorMap &map, const TcArgs &A, size_t smem, int nch, cudaStream_t s) {
-    auto kern = tc_kernel<BF16, G, MINB>;
+    auto kern = A.chain > 0 ? tc_kernel<BF16, G, MINB, true> : tc_kernel<BF16, G, MINB, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)n_tiles(A.g), (unsigned)nch);

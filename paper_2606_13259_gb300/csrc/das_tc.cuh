@@ -6,8 +6,11 @@
 
 namespace das {
 
-// Sub-items of one tensor-memory accumulation chain unless the tuning sets it.
+// Sub-items of one tensor-memory accumulation chain unless the tuning sets it
+// (applied to plans of at least TC_CHAIN_MIN_TX transmits, whose tiles sum
+// the most sub-items; one chain per tile otherwise).
 constexpr int TC_CHAIN_DEFAULT = 1024;
+constexpr int TC_CHAIN_MIN_TX = 4;
 
 // Arguments of the tensor-core forward kernel (das_tc.cu).
 struct TcArgs {

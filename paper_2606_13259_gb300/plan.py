@@ -126,8 +126,8 @@ class Plan:
                    load_width: int = 0, tensor_cores: bool = False, tc_chain: int = 0) -> None:
         """Kernel shape of the forward pass; tensor_cores selects the tcgen05
         contraction (IQ data with f16 / bf16 storage), tc_chain the MMA
-        sub-items per tensor-memory accumulation chain (0: automatic, -1: one
-        chain per tile)."""
+        sub-items per tensor-memory accumulation chain (0: automatic, 1024
+        with 4 or more transmits; -1: one chain per tile)."""
         t = L.Tuning(int(frames_per_thread), int(ctas_per_sm), 1 if staging else 0, int(load_width),
                      1 if tensor_cores else 0, int(tc_chain))
         L.check(self._lib.das_plan_set_tuning(self._h, C.byref(t)))
@@ -168,6 +168,18 @@ class Plan:
             raise ValueError(f"batch {B} outside 1..{self.max_batch}")
         return B
 
+    def _check_host(self, t: torch.Tensor, shape_tail, what: str) -> int:
+        if not isinstance(t, torch.Tensor) or t.device.type != "cpu":
+            raise ValueError(f"{what} must be a CPU tensor")
+        if t.dtype != self.data_dtype or not t.is_contiguous():
+            raise ValueError(f"{what} must be a contiguous {self.data_dtype} tensor")
+        if t.dim() < 1 or t.numel() != t.shape[0] * int(np.prod(shape_tail)):
+            raise ValueError(f"{what} must have shape (B, {', '.join(map(str, shape_tail))}), got {tuple(t.shape)}")
+        B = t.shape[0]
+        if not 1 <= B <= self.max_batch:
+            raise ValueError(f"batch {B} outside 1..{self.max_batch}")
+        return B
+
     # ------------------------------------------------------------------ compute
 
     def forward(self, y: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
@@ -183,13 +195,37 @@ class Plan:
     def forward_host(self, y: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
         """Host tensors in and out (copies inside the library call).  Buffers from
         host_empty keep the copies at link speed after long kernels."""
-        if y.device.type != "cpu" or not y.is_contiguous() or y.dtype != self.data_dtype:
-            raise ValueError("y must be a contiguous CPU tensor of the plan's data type")
-        B = y.shape[0]
+        B = self._check_host(y, (self.Q, self.M, self.K), "y")
         if out is None:
             out = host_empty((B,) + self.shape, self.data_dtype)
+        elif self._check_host(out, self.shape, "out") != B:
+            raise ValueError("out must hold as many frames as y")
         L.check(self._lib.das_forward_host(self._h, _ptr(y), _ptr(out), B, _stream(stream)))
         return out
+
+    def forward_host_many(self, ys: Sequence[torch.Tensor], outs: Optional[Sequence[torch.Tensor]] = None,
+                          stream=None) -> list:
+        """A sequence of host batches (equal frame counts) through the forward
+        pass, with each batch's copies overlapped with its neighbours' forward
+        passes.  Returns the host images (new host_empty buffers unless given)."""
+        ys = list(ys)
+        if not ys:
+            raise ValueError("no batches")
+        B = self._check_host(ys[0], (self.Q, self.M, self.K), "y")
+        if any(self._check_host(y, (self.Q, self.M, self.K), "y") != B for y in ys):
+            raise ValueError("every batch must hold the same number of frames")
+        if outs is None:
+            outs = [host_empty((B,) + self.shape, self.data_dtype) for _ in ys]
+        outs = list(outs)
+        if len(outs) != len(ys) or len({o.data_ptr() for o in outs}) != len(outs):
+            raise ValueError("one distinct output buffer per batch")
+        if any(self._check_host(o, self.shape, "out") != B for o in outs):
+            raise ValueError("outputs must hold as many frames as the batches")
+        n = len(ys)
+        yp = (C.c_void_p * n)(*[y.data_ptr() for y in ys])
+        xp = (C.c_void_p * n)(*[o.data_ptr() for o in outs])
+        L.check(self._lib.das_forward_host_many(self._h, yp, xp, n, B, _stream(stream)))
+        return outs
 
     def adjoint(self, x: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
         """image (B, nz, ny, nx) -> channel data (B, Q, M, K), the conjugate transpose of forward."""

@@ -87,6 +87,8 @@ def test_null_arguments_rejected(lib):
     assert L.das_adjoint(None, None, None, 1, None) == lib.DAS_ERR_INVALID_ARG
     assert L.das_grad_c(None, None, None, None, 1, None) == lib.DAS_ERR_INVALID_ARG
     assert L.das_plan_set_c(None, 1500.0) == lib.DAS_ERR_INVALID_ARG
+    assert L.das_forward_host(None, None, None, 1, None) == lib.DAS_ERR_INVALID_ARG
+    assert L.das_forward_host_many(None, None, None, 2, 1, None) == lib.DAS_ERR_INVALID_ARG
     L.das_plan_destroy(None)
 
 

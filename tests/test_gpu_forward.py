@@ -228,6 +228,31 @@ def test_forward_host_matches_device_call(das, kind):
     assert torch.equal(xh, ref)
 
 
+@pytest.mark.parametrize("n_batches,B", [(1, 5), (2, 5), (5, 3)])
+def test_forward_host_many_matches_device_calls(das, n_batches, B):
+    """A sequence of host batches with copies overlapped with the forward
+    passes (two staging slots): every image equals the device call's, for
+    sequences shorter than, equal to and longer than the two slots, and a
+    batch smaller than the plan's largest."""
+    sc = ragged_scene(*RAGGED[0])
+    plan = das.Plan.from_scene(sc, max_batch=5)
+    ys = [S.random_channels(sc, B, seed=40 + i) for i in range(n_batches)]
+    refs = [plan.forward(y.cuda()).cpu() for y in ys]
+    yh = []
+    for y in ys:
+        h = das.host_empty(y.shape, y.dtype)
+        h.copy_(y)
+        yh.append(h)
+    outs = plan.forward_host_many(yh)
+    # the same input buffer twice in one sequence
+    again = plan.forward_host_many([yh[0], yh[0]])
+    plan.check()
+    plan.close()
+    for o, r in zip(outs, refs):
+        assert torch.equal(o, r)
+    assert torch.equal(again[0], refs[0]) and torch.equal(again[1], refs[0])
+
+
 def test_host_empty_large_block_round_trip(das):
     """A block larger than one huge page survives a device round trip."""
     n = 3 * (1 << 27) + 12345  # ~ 1.5 GB of uint8 spread over several huge pages
