@@ -58,6 +58,28 @@ def parse_args():
     return ap.parse_args()
 
 
+def huge_page_fraction(t) -> "float | None":
+    """Share of a host tensor's resident pages that are transparent huge pages
+    (from /proc/self/smaps), None where unreadable."""
+    lo, hi = t.data_ptr(), t.data_ptr() + t.numel() * t.element_size()
+    rss = huge = 0
+    try:
+        cur = False
+        with open("/proc/self/smaps") as f:
+            for line in f:
+                head = line.split()
+                if "-" in head[0] and len(head) >= 5:
+                    a, b = (int(v, 16) for v in head[0].split("-"))
+                    cur = a < hi and b > lo
+                elif cur and head[0] == "Rss:":
+                    rss += int(head[1])
+                elif cur and head[0] == "AnonHugePages:":
+                    huge += int(head[1])
+    except (OSError, ValueError, IndexError):
+        return None
+    return huge / rss if rss else None
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -562,7 +584,8 @@ def main():
                "d2h_bytes_per_step": x_host.numel() * 8, "ms_per_step": dt * 1e3,
                "api": f"das_forward_host_many, {n_e2e} steps in one call (copies overlapped with forward passes)",
                "serial_value": world * F / dt_serial, "serial_api": "das_forward_host, one call per step",
-               "h2d_ms_torch_copy": h2d * 1e3, "d2h_ms_torch_copy": d2h * 1e3}
+               "h2d_ms_torch_copy": h2d * 1e3, "d2h_ms_torch_copy": d2h * 1e3,
+               "input_huge_page_fraction": huge_page_fraction(y_host)}
         del y_host, x_host, x_hosts
 
     peaks, peak_src = measured_peaks()

@@ -874,6 +874,12 @@ int das_forward_host_many(das_plan_t *plan, const void *const *y_host, void *con
     return DAS_OK;
 }
 
+#ifdef MADV_COLLAPSE
+#define DAS_MADV_COLLAPSE MADV_COLLAPSE
+#else
+#define DAS_MADV_COLLAPSE 25  // the Linux value of MADV_COLLAPSE
+#endif
+
 int das_host_alloc(size_t bytes, void **ptr) {
     g_err[0] = 0;
     if (!ptr) return fail(DAS_ERR_INVALID_ARG, "ptr is NULL");
@@ -894,6 +900,9 @@ int das_host_alloc(size_t bytes, void **ptr) {
     madvise(p, len, MADV_HUGEPAGE);  // advisory: small pages still work, only slower after GPU work
     const long page = sysconf(_SC_PAGESIZE) > 0 ? sysconf(_SC_PAGESIZE) : 4096;
     for (size_t o = 0; o < len; o += (size_t)page) p[o] = 0;  // fault the pages in before pinning
+    // where faulting gave small pages (fragmented memory), ask the kernel to
+    // collapse the range into huge pages now (Linux 6.1+; ignored elsewhere)
+    madvise(p, len, DAS_MADV_COLLAPSE);
     cudaError_t e = cudaHostRegister(p, len, cudaHostRegisterDefault);
     if (e != cudaSuccess) {
         cudaGetLastError();

@@ -2,7 +2,10 @@
 relative L2 and max-abs error (the largest |x - x_ref| over the largest
 |x_ref|, i.e. relative to the image peak), printed as one table row each and
 held to the bars of the forms (float32 1e-5, f16 2e-3, bf16 2e-2, E4M3 5e-2,
-relative L2).
+relative L2); and the peak-position error at the point targets: the voxel of
+the largest |x| near each target and its sub-voxel position (a parabola
+through the peak and its two neighbours along each axis), against the same
+on the oracle's image (the same voxel, positions within 0.1 voxel).
 
 Workloads: the small scene (32^3 voxels, 256 elements, RF and IQ, 2 frames),
 and sampled voxels of the paper workload (128^3 x 1024 x 16, 20 IQ frames)
@@ -36,6 +39,48 @@ def errors(x, ref):
     return rel, mx
 
 
+R = 3  # half width of the neighbourhood searched for a target's peak
+
+
+def neighbourhood(sc, p):
+    """Voxel indices of the (2R+1)^3 block around voxel p, in [z][y][x] order."""
+    ix, iy, iz = p
+    return np.array([sc.voxel_index(ix + dx, iy + dy, iz + dz) for dz in range(-R, R + 1)
+                     for dy in range(-R, R + 1) for dx in range(-R, R + 1)])
+
+
+def peak_position(a):
+    """|x| on a (2R+1)^3 block [z][y][x]: (x, y, z) of its peak relative to the
+    centre voxel, the largest value within the inner (2R-1)^3 voxels plus the
+    parabolic sub-voxel offset along each axis; and the integer voxel."""
+    inner = a[1:-1, 1:-1, 1:-1]
+    z, y, x = (int(i) + 1 for i in np.unravel_index(np.argmax(inner), inner.shape))
+    c = a[z, y, x]
+
+    def off(lo, hi):
+        den = lo - 2.0 * c + hi
+        return 0.5 * (lo - hi) / den if den < 0 else 0.0
+
+    pos = np.array([x - R + off(a[z, y, x - 1], a[z, y, x + 1]), y - R + off(a[z, y - 1, x], a[z, y + 1, x]),
+                    z - R + off(a[z - 1, y, x], a[z + 1, y, x])])
+    return pos, (x, y, z)
+
+
+def peak_errors(x_blocks, ref_blocks):
+    """Largest sub-voxel peak shift against the oracle (voxels, over targets and
+    frames), whether every integer peak voxel agrees, and the oracle's largest
+    peak offset from the target voxel itself."""
+    shift, same, truth = 0.0, True, 0.0
+    for xb, rb in zip(x_blocks, ref_blocks):
+        for f in range(xb.shape[0]):
+            p, v = peak_position(np.abs(xb[f]).reshape((2 * R + 1,) * 3))
+            q, w = peak_position(np.abs(rb[f]).reshape((2 * R + 1,) * 3))
+            shift = max(shift, float(np.max(np.abs(p - q))))
+            same = same and v == w
+            truth = max(truth, float(np.max(np.abs(q))))
+    return shift, same, truth
+
+
 def run(das, sc, y, storage, tc, voxels=None):
     B = y.shape[0]
     plan = das.Plan.from_scene(sc, storage=storage, max_batch=B)
@@ -58,9 +103,14 @@ CASES = [("small RF", False, "f32", False), ("small RF", False, "f16", False), (
 def test_small_scene_errors(das, oracle, name, iq, storage, tc):
     sc = S.scene_small_iq() if iq else S.scene_small()
     y = S.frames(sc, 2, seed=1, n_speckle=2000, points=S.SMALL_POINTS, noise_db=30.0)
-    rel, mx = errors(run(das, sc, y, storage, tc), oracle.forward(sc, y.numpy()))
-    print(f"\n| {name} | {'tensor cores' if tc else 'CUDA cores'} | {storage} | {rel:.2e} | {mx:.2e} |")
+    x, ref = run(das, sc, y, storage, tc), oracle.forward(sc, y.numpy())
+    rel, mx = errors(x, ref)
+    blocks = [neighbourhood(sc, p) for p in S.SMALL_POINTS]
+    shift, same, truth = peak_errors([x[:, b] for b in blocks], [ref[:, b] for b in blocks])
+    print(f"\n| {name} | {'tensor cores' if tc else 'CUDA cores'} | {storage} | {rel:.2e} | {mx:.2e} | "
+          f"{shift:.1e} | {truth:.2f} |")
     assert rel <= BAR[storage]
+    assert same and shift <= 0.1
 
 
 @pytest.mark.parametrize("workload,storage,tc", [("paper", "f32", False), ("paper", "f16", False),
@@ -72,7 +122,15 @@ def test_full_size_sampled_errors(das, oracle, workload, storage, tc):
     rng = np.random.default_rng(3)
     vox = np.concatenate([np.sort(rng.choice(sc.N, 64, replace=False)),
                           [sc.voxel_index(*p) for p in S.paper_points(sc)]])
-    x = run(das, sc, y, storage, tc, voxels=vox)
-    rel, mx = errors(x, oracle.forward(sc, y.cpu().numpy(), voxels=vox))
-    print(f"\n| {workload} (sampled) | {'tensor cores' if tc else 'CUDA cores'} | {storage} | {rel:.2e} | {mx:.2e} |")
+    blocks = [neighbourhood(sc, p) for p in S.paper_points(sc)]
+    allv = np.concatenate([vox] + blocks)
+    x = run(das, sc, y, storage, tc, voxels=allv)
+    ref = oracle.forward(sc, y[:2].cpu().numpy(), voxels=np.concatenate(blocks))  # peaks: first two frames
+    rel, mx = errors(x[:, :len(vox)], oracle.forward(sc, y.cpu().numpy(), voxels=vox))
+    nb = blocks[0].size
+    shift, same, truth = peak_errors([x[:2, len(vox) + i * nb:len(vox) + (i + 1) * nb] for i in range(len(blocks))],
+                                     [ref[:, i * nb:(i + 1) * nb] for i in range(len(blocks))])
+    print(f"\n| {workload} (sampled) | {'tensor cores' if tc else 'CUDA cores'} | {storage} | {rel:.2e} | {mx:.2e} | "
+          f"{shift:.1e} | {truth:.2f} |")
     assert rel <= BAR[storage]
+    assert same and shift <= 0.1
