@@ -15,6 +15,7 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
 using namespace das;
@@ -797,11 +798,17 @@ int das_forward_host(das_plan_t *plan, const void *y_host, void *x_host, int bat
     if ((rc = ensure_host_io(plan, 1)) != DAS_OK) return rc;
     const size_t yb = (size_t)batch * plan->Q * plan->M * plan->K * sample_bytes_public(plan);
     const size_t xb = (size_t)batch * plan->g.n_voxels * sample_bytes_public(plan);
-    if ((rc = copy_split(plan, plan->stage_y[0], y_host, yb, cudaMemcpyHostToDevice, s)) != DAS_OK) return rc;
-    if ((rc = das_forward(plan, plan->stage_y[0], plan->stage_x[0], batch, stream)) != DAS_OK) return rc;
-    if ((rc = copy_split(plan, x_host, plan->stage_x[0], xb, cudaMemcpyDeviceToHost, s)) != DAS_OK) return rc;
-    DAS_CU(cudaStreamSynchronize(s));
-    return DAS_OK;
+    if ((rc = copy_split(plan, plan->stage_y[0], y_host, yb, cudaMemcpyHostToDevice, s)) == DAS_OK &&
+        (rc = das_forward(plan, plan->stage_y[0], plan->stage_x[0], batch, stream)) == DAS_OK &&
+        (rc = copy_split(plan, x_host, plan->stage_x[0], xb, cudaMemcpyDeviceToHost, s)) == DAS_OK) {
+        DAS_CU(cudaStreamSynchronize(s));
+        return DAS_OK;
+    }
+    // copies already queued use the caller's host buffers: let them finish first
+    const std::string first = g_err;
+    for (cudaStream_t cs : plan->copy_streams) cudaStreamSynchronize(cs);
+    cudaStreamSynchronize(s);
+    return fail(rc, "%s", first.c_str());
 }
 
 // `bytes` as up to HOST_COPY_STREAMS pieces (at least 16 MB each) on the copy
@@ -829,17 +836,10 @@ static int copy_pieces(das_plan *p, void *dst, const void *src, size_t bytes, cu
     return DAS_OK;
 }
 
-int das_forward_host_many(das_plan_t *plan, const void *const *y_host, void *const *x_host, int n_batches,
-                          int batch, das_stream_t stream) {
-    g_err[0] = 0;
-    if (!plan || !y_host || !x_host) return fail(DAS_ERR_INVALID_ARG, "NULL argument");
-    if (n_batches < 1) return fail(DAS_ERR_INVALID_ARG, "n_batches must be >= 1");
+// The work of das_forward_host_many after its checks (see there).
+static int forward_host_many_run(das_plan *plan, const void *const *y_host, void *const *x_host, int n_batches,
+                                 int batch, cudaStream_t s) {
     int rc;
-    for (int i = 0; i < n_batches; ++i)
-        if ((rc = check_call(plan, y_host[i], x_host[i], batch)) != DAS_OK) return rc;
-    DeviceGuard guard(plan->device);
-    cudaStream_t s = (cudaStream_t)stream;
-    if ((rc = ensure_host_io(plan, 2)) != DAS_OK) return rc;
     const size_t yb = (size_t)batch * plan->Q * plan->M * plan->K * sample_bytes_public(plan);
     const size_t xb = (size_t)batch * plan->g.n_voxels * sample_bytes_public(plan);
     int n_in[2] = {0, 0}, n_out[2] = {0, 0};
@@ -860,7 +860,7 @@ int das_forward_host_many(das_plan_t *plan, const void *const *y_host, void *con
         // forward pass of batch i once its inputs are in and slot j's image of batch i - 2 is out
         for (int k = 0; k < n_in[j]; ++k) DAS_CU(cudaStreamWaitEvent(s, plan->in_done[j][k], 0));
         for (int k = 0; k < n_out[j]; ++k) DAS_CU(cudaStreamWaitEvent(s, plan->out_done[j][k], 0));
-        if ((rc = das_forward(plan, plan->stage_y[j], plan->stage_x[j], batch, stream)) != DAS_OK) return rc;
+        if ((rc = das_forward(plan, plan->stage_y[j], plan->stage_x[j], batch, s)) != DAS_OK) return rc;
         DAS_CU(cudaEventRecord(plan->fwd_done[j], s));
         used[j] = true;
         // image of batch i out while batch i + 1 runs
@@ -872,6 +872,29 @@ int das_forward_host_many(das_plan_t *plan, const void *const *y_host, void *con
         for (int k = 0; k < n_out[j]; ++k) DAS_CU(cudaStreamWaitEvent(s, plan->out_done[j][k], 0));
     DAS_CU(cudaStreamSynchronize(s));
     return DAS_OK;
+}
+
+int das_forward_host_many(das_plan_t *plan, const void *const *y_host, void *const *x_host, int n_batches,
+                          int batch, das_stream_t stream) {
+    g_err[0] = 0;
+    if (!plan || !y_host || !x_host) return fail(DAS_ERR_INVALID_ARG, "NULL argument");
+    if (n_batches < 1) return fail(DAS_ERR_INVALID_ARG, "n_batches must be >= 1");
+    int rc;
+    for (int i = 0; i < n_batches; ++i)
+        if ((rc = check_call(plan, y_host[i], x_host[i], batch)) != DAS_OK) return rc;
+    DeviceGuard guard(plan->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((rc = ensure_host_io(plan, 2)) != DAS_OK) return rc;
+    rc = forward_host_many_run(plan, y_host, x_host, n_batches, batch, s);
+    if (rc != DAS_OK) {
+        // copies already queued read or write the caller's host buffers: let
+        // them finish before returning (the error text stays the first one)
+        const std::string first = g_err;
+        for (cudaStream_t cs : plan->copy_streams) cudaStreamSynchronize(cs);
+        cudaStreamSynchronize(s);
+        fail(rc, "%s", first.c_str());
+    }
+    return rc;
 }
 
 #ifdef MADV_COLLAPSE
