@@ -294,7 +294,7 @@ size_t tc_scratch_bytes(const das_plan *p) {
     size_t best = 0;
     for (int B = 1; B <= p->max_batch; ++B) {
         int bc, nch, n;
-        tc_shape(B, bc, nch, n);
+        tc_shape(B, tc_max_frames(p->tuning.ctas_per_sm), bc, nch, n);
         const size_t b = (size_t)nch * p->Q * p->M * (size_t)n * p->K * 4;
         best = b > best ? b : best;
     }
@@ -325,7 +325,7 @@ int ensure_tc_scratch(das_plan *p) {
 // then the tcgen05 kernel (das_tc.cu).
 int forward_tc(das_plan *p, const void *y, void *x, int B, cudaStream_t s) {
     int bc, nch, n;
-    tc_shape(B, bc, nch, n);
+    tc_shape(B, tc_max_frames(p->tuning.ctas_per_sm), bc, nch, n);
     const int QM = p->Q * p->M;
     const size_t need = (size_t)nch * QM * (size_t)n * p->K * 4;
     if (need > p->z_tc_bytes || !p->ratio || !p->smax)

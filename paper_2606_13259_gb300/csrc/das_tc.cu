@@ -861,8 +861,8 @@ __global__ void __launch_bounds__(128) tc_relayout_kernel(const float2 *__restri
     }
 }
 
-void tc_shape(int B, int &bc, int &nch, int &n) {
-    nch = (B + 127) / 128;
+void tc_shape(int B, int max_bc, int &bc, int &nch, int &n) {
+    nch = (B + max_bc - 1) / max_bc;
     bc = (B + nch - 1) / nch;
     n = ((2 * bc + 15) / 16) * 16;
 }

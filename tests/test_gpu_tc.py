@@ -60,12 +60,14 @@ def test_ragged_tiles_and_transmit_kinds(das, oracle, case, B):
     assert rel_l2(x, oracle.forward(sc, y.numpy())) <= TOL["f16"]
 
 
-@pytest.mark.parametrize("B", [16, 128, 130])
-def test_mma_widths_and_frame_chunks(das, oracle, B):
-    """N = 32 and the largest N = 256 (128 frames), and two frame chunks (130 frames)."""
+@pytest.mark.parametrize("B,ctas", [(16, 0), (128, 0), (130, 0), (128, 2), (130, 2), (112, 2)])
+def test_mma_widths_and_frame_chunks(das, oracle, B, ctas):
+    """N = 32 and the largest N = 256 (128 frames), and two frame chunks (130
+    frames); with two CTAs per SM at most 112 frames per chunk (128 frames:
+    two chunks of 64, N = 128; 112 frames: one chunk, N = 224)."""
     sc = ragged_scene(*RAGGED[0])
     y = S.random_channels(sc, B, seed=B)
-    x = tc_forward(das, sc, y).cpu().numpy()
+    x = tc_forward(das, sc, y, ctas_per_sm=ctas).cpu().numpy()
     assert rel_l2(x, oracle.forward(sc, y.numpy())) <= TOL["f16"]
 
 
