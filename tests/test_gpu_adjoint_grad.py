@@ -40,6 +40,22 @@ def test_adjoint_matches_oracle(das, oracle, case, B):
     plan.close()
 
 
+@pytest.mark.parametrize("B", [9, 45])
+def test_adjoint_and_grad_c_large_batches(das, oracle, B):
+    """Batches that span several frame chunks of the adjoint and of the
+    derivative kernel (ragged last chunk)."""
+    sc = ragged_scene(*RAGGED[0])
+    x = image_like(sc, B, seed=50 + B)
+    y = S.random_channels(sc, B, seed=60 + B)
+    plan = das.Plan.from_scene(sc, max_batch=B)
+    ya = plan.adjoint(x.cuda().reshape((B,) + plan.shape)).cpu().numpy()
+    assert rel_l2(ya, oracle.adjoint(sc, x.numpy()).reshape(ya.shape)) <= TOL_F32
+    got = float(plan.grad_c(y.cuda(), x.cuda().reshape((B,) + plan.shape)))
+    ref = oracle.grad_c(sc, y.numpy(), x.numpy())
+    assert abs(got - ref) <= 1e-4 * abs(ref)
+    plan.close()
+
+
 @pytest.mark.parametrize("iq", [False, True])
 def test_adjoint_small_and_dot_product(das, oracle, iq):
     """Full-size small scene, and <A y, x> = <y, A^H x> with both maps on the GPU."""

@@ -102,6 +102,17 @@ def test_frames_per_thread_variants(das, oracle, fb):
     assert rel_l2(x, ref) <= TOL_F32
 
 
+@pytest.mark.parametrize("B,storage,tol", [(45, "f32", 1e-5), (130, "f32", 1e-5), (45, "f16", 2e-3),
+                                           (130, "bf16", 2e-2)])
+def test_large_batches_in_several_frame_chunks(das, oracle, B, storage, tol):
+    """Batches of several frame chunks with a ragged last one (45 frames: 20 +
+    20 + 5 with float32 rows) and a large batch (130 frames), default widths."""
+    sc = ragged_scene(*RAGGED[0])
+    y = S.random_channels(sc, B, seed=B + 100)
+    x = run_forward(das, sc, y, storage=storage)
+    assert rel_l2(x, oracle.forward(sc, y.numpy())) <= tol
+
+
 def test_transmit_weights(das, oracle):
     sc = ragged_scene(*RAGGED[0])
     rng = np.random.default_rng(2)
