@@ -28,6 +28,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "volumes/s, forward DAS at 128^3 voxels x 1024 elements x 16 transmits (IQ, float32)"
+
+
+def metric_for(storage: str, tensor_cores: bool) -> str:
+    """The metric text of a paper-workload line: the storage and path it ran."""
+    if storage == "f32" and not tensor_cores:
+        return METRIC
+    path = ", tensor cores" if tensor_cores else ""
+    return METRIC.replace("(IQ, float32)", f"(IQ, {storage} storage{path})")
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
@@ -609,7 +617,8 @@ def main():
             "work_per_launch": f"{active} contributing terms x {F} frames x 16 flop"}
 
     line = {
-        "metric": METRIC, "value": world * F / (ms * 1e-3), "unit": "volumes/s", "n_gpus": world,
+        "metric": metric_for(args.storage, args.tensor_cores), "value": world * F / (ms * 1e-3), "unit": "volumes/s",
+        "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.storage == "f32" else args.storage,
         "data": "synthetic (seeded speckle + 10 point targets, time-domain simulator)",
