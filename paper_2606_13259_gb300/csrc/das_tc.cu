@@ -252,8 +252,20 @@ __device__ __forceinline__ int tc_item(int tb, int rb, float rf, float tmin, flo
 // ---------------------------------------------------------------------------
 
 struct TcSmem {
-    size_t bars, misc, list, lw, eg, en, gb, erb, em, t, w, tb, tmin, tmax, total;
+    size_t bars, misc, sel, list, lw, eg, en, gb, erb, em, t, w, tb, tmin, tmax, total;
 };
+
+// Rows of the byte-permute selectors that place a W row's two values: for a
+// window offset u (0 .. TC_KV - 1) and word c of a 16-value plane, the bytes of
+// the 32-bit word (value u, value u + 1) that word c takes (0x44: zero
+// bytes).  Row TC_KV: all words zero (an inactive voxel).
+constexpr int TC_SEL_ROWS = TC_KV + 1;
+__host__ __device__ inline uint32_t tc_sel(int u, int c) {
+    if (u >= TC_KV) return 0x4444u;
+    if (c == (u >> 1)) return (u & 1) ? 0x1044u : 0x3210u;  // (u, u+1) in word c, or u in its upper half
+    if ((u & 1) && c == (u >> 1) + 1) return 0x4432u;      // u + 1 in the lower half of the next word
+    return 0x4444u;
+}
 
 // Shared memory of one CTA: sb window stages, barriers, the element records
 // of one block of eb elements and a sub-item list of list_cap entries.
@@ -262,6 +274,7 @@ __host__ __device__ inline TcSmem tc_smem_layout(int sb, int n, int Q, bool has_
     size_t o = (size_t)sb * 64 * n;  // window stages (1024-aligned base)
     L.bars = o; o += 128 * 8;
     L.misc = o; o += 128 * 4;
+    L.sel = o; o += (size_t)TC_SEL_ROWS * 8 * 4;
     L.list = o; o += (size_t)list_cap * 8;
     L.lw = o; o += (size_t)list_cap * 4;
     L.eg = o; o += (size_t)eb * 16;
@@ -366,6 +379,7 @@ __global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_co
     int *s_tb = reinterpret_cast<int *>(smem + L.tb);
     float *s_tmin = reinterpret_cast<float *>(smem + L.tmin);
     float *s_tmax = reinterpret_cast<float *>(smem + L.tmax);
+    uint32_t *s_sel = reinterpret_cast<uint32_t *>(smem + L.sel);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int vl = tid & (TILE_N - 1);  // voxel lane = TMEM lane of a builder thread
@@ -400,6 +414,7 @@ __global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_co
             if (has_w) s_w[q * TILE_N + tid] = A.w_tx[(tile * Q + q) * TILE_N + tid];
         }
     }
+    for (int i = tid; i < TC_SEL_ROWS * 8; i += tc_threads(G)) s_sel[i] = tc_sel(i >> 3, i & 7);
     for (int q = tid; q < Q; q += tc_threads(G)) {
         s_tb[q] = A.tx_tb[tile * Q + q];
         s_tmin[q] = A.tx_tmin[tile * Q + q];
@@ -624,19 +639,17 @@ __global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_co
                     const float w0 = w * (1.f - al), w1 = w * al;
                     const uint32_t pr = pack2<BF16>(w0 * uhr, w1 * ubr);  // (Wr[u], Wr[u+1])
                     const uint32_t pi = pack2<BF16>(w0 * uhi, w1 * ubi);  // (Wi[u], Wi[u+1])
+                    // the row: (value u, value u + 1) of each plane at 16-bit position u,
+                    // zeros elsewhere, by byte permutes with the selectors of row u
                     const bool in = act && (unsigned)u < (unsigned)TC_KV;
-                    const int uw = in ? (u >> 1) : -8;
-                    const bool odd = (u & 1) != 0;
-                    const uint32_t Pr = odd ? (pr << 16) : pr, Qr = odd ? (pr >> 16) : 0u;
-                    const uint32_t Pi = odd ? (pi << 16) : pi, Qi = odd ? (pi >> 16) : 0u;
+                    const uint4 *sel = reinterpret_cast<const uint4 *>(s_sel + 8 * (in ? u : TC_KV));
+                    const uint4 s0 = sel[0], s1 = sel[1];
+                    const uint32_t sw[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
                     uint32_t v[16];
-                    bool prev = false;  // word c - 1 holds the first value
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {
-                        const bool e0 = c == uw;
-                        v[c] = e0 ? Pr : (prev ? Qr : 0u);
-                        v[8 + c] = e0 ? Pi : (prev ? Qi : 0u);
-                        prev = e0;
+                        v[c] = __byte_perm(pr, 0u, sw[c]);
+                        v[8 + c] = __byte_perm(pi, 0u, sw[c]);
                     }
                     // the group's previous store has drained while v was built: signal it
                     tmem_st_wait();
