@@ -31,8 +31,8 @@
  * pointers are host memory owned by the caller.  The plan owns its own device
  * buffers (geometry, per-tile reference delays, channel-data relayout scratch)
  * and allocates them only in das_plan_create, das_plan_set_tuning (when a
- * tuning needs more scratch) and the first das_forward_host call; the other
- * compute calls allocate nothing.  Calls are asynchronous on the given stream unless
+ * tuning needs more scratch) and the first das_forward_host /
+ * das_forward_host_many call; the other compute calls allocate nothing.  Calls are asynchronous on the given stream unless
  * stated otherwise; a plan must not be used by two streams at once.
  *
  * Errors: every function returns DAS_OK (0) or a DAS_ERR_* code.  Invalid
