@@ -33,6 +33,12 @@ MUTANTS = {
     "aperture_margin_inverted": ("(1.0 + APERTURE_MARGIN) * half_width", "(1.0 - APERTURE_MARGIN) * half_width"),
     "transmit_weight_transposed": ("P->w_tx[(long)q * n_voxels(P) + n]", "P->w_tx[(long)n * P->Q + q]"),
     "plane_wave_sign_flipped": ("return (v[0] * (p[0] - P->t0_ref[0])", "return -(v[0] * (p[0] - P->t0_ref[0])"),
+    "count_active_first_transmit_only": ("        for (int q = 0; q < P->Q; ++q)\n            for (int m",
+                                         "        for (int q = 0; q < 1; ++q)\n            for (int m"),
+    "count_active_drops_first_element": ("if (term(P, q, m, n, p, &k, &alpha, &ts, &w)) ++count;",
+                                         "if (term(P, q, m, n, p, &k, &alpha, &ts, &w) && m > 0) ++count;"),
+    "near_ties_count_exact_ties": ("if (d > 1e-9 * thr && d <= rel * thr) ++count;", "if (d <= rel * thr) ++count;"),
+    "near_ties_half_width_wrong": ("double hw = z / (2.0 * P->f_number);", "double hw = z / (P->f_number);"),
 }
 
 

@@ -171,6 +171,48 @@ def test_small_scene_has_no_near_ties(oracle):
     assert oracle.count_near_ties(S.scene_small(), 1e-5) == 0
 
 
+def test_count_active_small_scene_is_lattice_count(oracle):
+    """Every delay of the small scene lies in range (K = 512; with K = 4096 also
+    for a second, laterally shifted source), so the number of contributing
+    terms is Q times the exact integer count of aperture elements summed over
+    the voxels (Eq. 2 with the range rule of the text after it)."""
+    sc = S.scene_small()
+    per_tx = int(lattice_counts_small().sum())
+    assert oracle.count_active(sc) == per_tx
+    two = sc.with_(K=4096, tx_kind=np.array([0, 0], np.int32),
+                   tx_vec=np.array([[0.0, 0.0, -10 * MM], [1.0 * MM, 0.0, -10 * MM]]))
+    assert oracle.count_active(two) == 2 * per_tx
+
+
+@pytest.mark.parametrize("K,count", [(489, 8), (488, 4), (372, 4), (371, 0)])
+def test_count_active_range_edges(oracle, K, count):
+    """Ring scene: voxel (0, 0, 12) mm, four elements on a 5 mm ring (receive
+    path 13 mm) inside the f-number-1 aperture and one at 7 mm outside it;
+    source (0, 0, -5) mm gives the path 12 + 13 = 25 mm, i.e. tau fs =
+    750000 / 1540 = 487.01 (k = 487), source (9, 0, 0) mm gives 6 + 13 = 19 mm,
+    i.e. 570000 / 1540 = 370.13 (k = 370).  A term counts when k <= K - 2."""
+    ring = [(3, 4, 0), (-4, 3, 0), (5, 0, 0), (0, -5, 0)]
+    sc = one_voxel((0, 0, 12), ring + [(7, 0, 0)],
+                   [(S.TX_DIVERGING, (0, 0, -5)), (S.TX_DIVERGING, (9, 0, 0))], f_number=1.0, K=K)
+    assert oracle.count_active(sc) == count
+
+
+def test_count_near_ties_hand_built(oracle):
+    """Voxel (0, 0, 12) mm at f-number 1.2: the aperture half width is exactly
+    5 mm.  The four ring elements sit exactly on it (ties, never counted), one
+    element is 1e-7 off in rho^2 (5 (1 + 5e-8) mm), one about 4e-5 off
+    (5.0001 mm) and one far inside (3 mm, rho^2 off by 0.64)."""
+    ring = [(3, 4, 0), (-4, 3, 0), (5, 0, 0), (0, -5, 0)]
+    near = [(5 * (1 + 5e-8), 0, 0), (-5.0001, 0, 0), (0, 3, 0)]
+    sc = one_voxel((0, 0, 12), ring + near, [(S.TX_DIVERGING, (0, 0, -5))], f_number=1.2)
+    assert oracle.count_near_ties(sc, 1e-5) == 1
+    assert oracle.count_near_ties(sc, 1e-4) == 2
+    assert oracle.count_near_ties(sc, 1.0) == 3
+    assert oracle.count_near_ties(one_voxel((0, 0, 12), ring, [(S.TX_DIVERGING, (0, 0, -5))],
+                                            f_number=1.2), 1.0) == 0
+    assert oracle.count_near_ties(sc.with_(f_number=0.0), 1.0) == 0
+
+
 # ---------------------------------------------------------------- point reflectors
 
 def test_point_reflectors_peak_at_their_voxels(oracle):
