@@ -36,8 +36,19 @@ def metric_for(storage: str, tensor_cores: bool) -> str:
         return METRIC
     path = ", tensor cores" if tensor_cores else ""
     return METRIC.replace("(IQ, float32)", f"(IQ, {storage} storage{path})")
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
+
+
+def sm_count(device=0) -> int:
+    """Streaming multiprocessors of the device (cudaDevAttrMultiProcessorCount)."""
+    import torch
+
+    return int(torch.cuda.get_device_properties(device).multi_processor_count)
+
+
+def fp32_peak_tflops(sm_max_mhz: float, device=0) -> float:
+    """FP32 FMA peak: SMs x 128 lanes x 2 flop x the maximum SM clock."""
+    return sm_count(device) * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
 
 
 def parse_args():
@@ -104,23 +115,31 @@ def apply_tuning(plan, args) -> None:
 
 
 def tensor_roofline(plan, items0: int, launches: int, kern_ms: float, storage: str, profile: str,
-                    items1: "int | None" = None) -> dict:
-    """Tensor-pipe roofline of the tcgen05 kernel: MMA flops issued per launch
-    (sub-items x 2 x 128 x N x 32, counted by the kernel between the counter
-    readings items0 and items1, the timed launches) over its event time,
-    against the measured sustained dense bf16 (= f16) rate."""
+                    useful_flops: float, work_text: str, items1: "int | None" = None) -> dict:
+    """Tensor-pipe roofline of the tcgen05 kernel.  `frac` counts the method's
+    work (contributing terms x frames x 16 flop, the complex two-tap
+    interpolation and rotation of Eq. 2) over the kernel's event time against
+    the measured sustained dense bf16 (= f16) rate.  The MMA flops the kernel
+    issues (sub-items x 2 x 128 x N x 32, counted by the kernel between the
+    counter readings items0 and items1, the timed launches) include the zero
+    rows of each weight window and the padded columns of N; they are reported
+    beside it as `mma_issue_frac`."""
     peaks, src = measured_peaks()
     info = plan.info()
     items = ((info["tc_mma_items"] if items1 is None else items1) - items0) / max(launches, 1)
     n = info["tc_mma_n"]
-    flops = items * 2.0 * 128 * n * 32
-    achieved = flops / (kern_ms * 1e-3) / 1e12
+    issued = items * 2.0 * 128 * n * 32
+    achieved = useful_flops / (kern_ms * 1e-3) / 1e12
+    issued_t = issued / (kern_ms * 1e-3) / 1e12
     peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1700.0)))
     return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": profiled_traffic(storage, profile, TC_SOURCES),
             "kernel": "tc_kernel (tcgen05 tile contraction)", "kernel_ms": kern_ms,
             "peak_source": f"{src} dense bf16 sustained (f16 runs at the same rate)",
-            "work_per_launch": f"{items:.0f} MMA sub-items x 128 x {n} x 32 x 2 flop"}
+            "work_per_launch": work_text,
+            "mma_issue_tflops": issued_t, "mma_issue_frac": issued_t / peak,
+            "mma_issued_per_launch": f"{items:.0f} MMA sub-items x 128 x {n} x 32 x 2 flop",
+            "dense_to_useful": issued / useful_flops if useful_flops else None}
 
 
 TILE_SOURCES = ("das_tile.cuh", "das_tile_tma.cuh", "das_tile_f32.cu", "das_internal.cuh")
@@ -344,7 +363,7 @@ def run_batched(args):
     actives = [p.count_active() for p in plans]
     flops = sum(a * f * 16.0 for a, f in zip(actives, frames))
     sm_max = float(measured_peaks()[0].get("sm_max_mhz", 2070.0))
-    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    fp32_peak = fp32_peak_tflops(sm_max)
     line = {
         "metric": "volumes/s, batched forward DAS over 3 uneven plans in one persistent launch (FP16 IQ storage)",
         "value": total / (ms * 1e-3), "unit": "volumes/s", "n_gpus": 1, "steps": args.steps,
@@ -406,15 +425,17 @@ def run_table1(args):
     kms, kn = plan.timing()
     kern_ms = kms / max(kn, 1)
     sm_max = float(measured_peaks()[0].get("sm_max_mhz", 2070.0))
-    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    fp32_peak = fp32_peak_tflops(sm_max)
     flops = active * F * 16.0
+    work = f"{active} contributing terms x {F} frames x 16 flop"
     line = {
         "metric": "volumes/s, forward DAS in the paper's Table 1 configuration (B 128, M 1024, Q 1, K 256, N 128^3)",
         "value": F / (ms * 1e-3), "unit": "volumes/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": args.storage + " storage, f32 arithmetic", "data": "synthetic",
         "config": {"workload": sc.name, "frames_per_step": F, "scene": sc.describe()},
-        "roofline": tensor_roofline(plan, items0, kn, kern_ms, args.storage, "tc_kernel_table1") if args.tensor_cores else
+        "roofline": tensor_roofline(plan, items0, kn, kern_ms, args.storage, "tc_kernel_table1", flops, work)
+        if args.tensor_cores else
         {"bound": "alu", "achieved": flops / (kern_ms * 1e-3) / 1e12, "peak": fp32_peak,
          "unit": "TFLOP/s", "frac": flops / (kern_ms * 1e-3) / 1e12 / fp32_peak, "traffic": None,
          "kernel_ms": kern_ms},
@@ -602,23 +623,27 @@ def main():
 
     peaks, peak_src = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    sms = sm_count(dev)
+    fp32_peak = fp32_peak_tflops(sm_max, dev)
     flops = active * F * 16.0          # 8 FMA per contributing (voxel, element, transmit, frame) term
+    work = f"{active} contributing terms x {F} frames x 16 flop"
     achieved = flops / (kern_ms * 1e-3) / 1e12
     bytes_store = {"f32": 8, "f16": 4, "bf16": 4, "e4m3": 2}[args.storage]
     alg_bytes = sc.Q * sc.M * sc.K * F * bytes_store + F * sc.N * 8
     if args.tensor_cores:
-        roof = tensor_roofline(plan, items0, kern_n, kern_ms, args.storage, "tc_kernel_paper_iq", items1)
-        roof.update({"useful_flops_tflops": achieved, "hbm_algorithmic_gbs": alg_bytes / (kern_ms * 1e-3) / 1e9})
+        roof = tensor_roofline(plan, items0, kern_n, kern_ms, args.storage, "tc_kernel_paper_iq", flops, work,
+                               items1)
+        roof.update({"hbm_algorithmic_gbs": alg_bytes / (kern_ms * 1e-3) / 1e9, "sm_count": sms})
     else:
         roof = None
     roof = roof or {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
             "frac": achieved / fp32_peak, "traffic": profiled_traffic(args.storage),
             "kernel": "tile_kernel (forward DAS)", "kernel_ms": kern_ms,
-            "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz ({peak_src} max SM clock)",
+            "peak_source": f"{sms} SMs (device attribute) x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
+                           f"({peak_src} max SM clock)",
             "hbm_algorithmic_gbs": alg_bytes / (kern_ms * 1e-3) / 1e9,
             "hbm_peak_gbs": float(peaks.get("hbm_gbs", 6800.0)),
-            "work_per_launch": f"{active} contributing terms x {F} frames x 16 flop"}
+            "work_per_launch": work}
 
     line = {
         "metric": metric_for(args.storage, args.tensor_cores), "value": world * F / (ms * 1e-3), "unit": "volumes/s",
@@ -633,7 +658,11 @@ def main():
                    "frames_per_thread": args.fb or "auto", "tensor_cores": bool(args.tensor_cores),
                    **({"tc_chain": args.tc_chain or "auto"} if args.tensor_cores else {})},
         "accumulations_per_s": world * F * sc.N * sc.M * sc.Q / (ms * 1e-3),
+        "accumulations_note": "accumulations_per_s counts the dense N x M x Q terms per volume (the paper's "
+                              "3.4e10); contributing_terms_per_s counts those inside the f-number aperture and "
+                              "the sample range, the work the roofline uses",
         "contributing_terms_per_volume": active,
+        "contributing_terms_per_s": world * F * active / (ms * 1e-3),
         "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

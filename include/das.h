@@ -134,7 +134,11 @@ typedef struct {
     int staging;           /* 1: stage each (element, transmit) window of sample rows in shared
                               memory with bulk asynchronous copies; 0: read rows straight from
                               global memory (default) */
-    int load_width;        /* bits per lane of each global sample load: 128 (default) or 256 */
+    int load_width;        /* how the kernels read sample rows from global memory: 0 (default)
+                              column order, each row cut into 16-byte pieces stored along k so
+                              that lanes with nearby delays share 128-byte lines (rows that are
+                              not whole 16-byte pieces, and staged windows, use row order);
+                              128 or 256: row order with loads of that many bits per lane */
     int tensor_cores;      /* 1: forward pass as a tensor-core contraction (Sec. 3.4 tile
                               reformulation on tcgen05 MMAs, IQ data with DAS_STORE_F16 or
                               DAS_STORE_BF16 only; the weights are rounded to the storage
@@ -238,11 +242,15 @@ int das_grad_c(das_plan_t *plan, const void *y_dev, const void *gx_dev, double *
  * thread)) are rejected with DAS_ERR_UNSUPPORTED before any launch.  The first
  * call on a device looks up the array's device address (cudaGetSymbolAddress)
  * with that device current; make that first call before any stream capture.
+ * The address is kept for the life of the process: after a reset of the
+ * device's primary context (cudaDeviceReset) the library must be unloaded
+ * and loaded again before this entry point is called.
  * No slot needs clearing: each is written in the call before it is read.  All
  * calls share the one array, so calls that overlap on the GPU (other streams,
  * other threads) race and must be serialised by the caller.  The plan's
- * relayout scratch for IQ data is used as in das_grad_c (allocated when the
- * plan was created). */
+ * channel-data scratch is used as in das_grad_c (allocated when the plan was
+ * created): for IQ data, and for RF data of more than one frame.  Like every
+ * call on a plan, calls on one plan must not overlap. */
 int das_grad_c_static(das_plan_t *plan, const void *y_dev, const void *gx_dev, double *dLdc_dev, int batch,
                       das_stream_t stream);
 

@@ -102,10 +102,11 @@ def _apply(plan: Plan, cfg: dict) -> None:
 
 
 def tune_plan(plan: Plan, y, out, fbs: Optional[Iterable[int]] = None, staging=(False, True),
-              load_widths=(128, 256), tensor_cores=(False, True), reps: int = 3, warmup: int = 1,
+              load_widths=(0, 128, 256), tensor_cores=(False, True), reps: int = 3, warmup: int = 1,
               use_cache: bool = True) -> dict:
     """Pick the forward kernel of single-plan calls: CUDA-core tile kernel
-    (frames per thread, staged windows, load width) or the tensor-core tile
+    (frames per thread, staged windows, row load: 0 column order, 128 / 256
+    row order with that load width) or the tensor-core tile
     contraction (CTAs per SM), the latter for IQ plans with 16-bit storage."""
     B = y.shape[0]
     key = "plan:" + torch.cuda.get_device_name() + ":" + _plan_sig(plan) + f"/B{B}"

@@ -261,9 +261,17 @@ TileArgs tile_args(const das_plan *p, int B, int fb, const void *z) {
 
 bool aligned(const void *ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
 
+// Whether the tile kernels of a call with `fb` frames per thread read the
+// relayouted rows in column order (LD_COL in das_tile.cuh): the default load
+// path, unless a tuning asks for staged windows or a fixed row load width.
+int col_layout(const das_plan *p, int fb) {
+    return (!p->tuning.staging && p->tuning.load_width == 0 && tile_col_supported(is_iq(p), p->storage, fb)) ? 1 : 0;
+}
+
 // Relayout of the public channel data into the plan scratch (or the data
-// itself when the layouts coincide).  Returns the pointer the kernels read.
-int stage_channels(das_plan *p, const void *y, int B, int fb, int nch, cudaStream_t s, const void **z_out) {
+// itself when the layouts coincide), in column order when `col`.  Returns the
+// pointer the kernels read.
+int stage_channels(das_plan *p, const void *y, int B, int fb, int nch, int col, cudaStream_t s, const void **z_out) {
     const int Bs = fb * nch;
     const bool iq = is_iq(p);
     const int QM = p->Q * p->M;
@@ -271,14 +279,14 @@ int stage_channels(das_plan *p, const void *y, int B, int fb, int nch, cudaStrea
         DAS_CU(launch_scale(y, p->scale, p->inv_scale, iq, p->storage, B, QM, p->K, s));
         p->launches += 1;
     }
-    if (!iq && p->storage == DAS_STORE_F32 && Bs == 1) {
+    if (!iq && p->storage == DAS_STORE_F32 && Bs == 1 && !col) {
         *z_out = y;
         return DAS_OK;
     }
     const size_t need = (size_t)QM * p->K * (size_t)Bs * sample_bytes_store(p);
     if (need > p->z_bytes) return fail(DAS_ERR_INVALID_ARG, "batch needs %zu bytes of scratch, plan holds %zu", need, p->z_bytes);
     DAS_CU(launch_relayout(y, p->z, iq ? p->rot : nullptr, p->storage == DAS_STORE_F32 ? nullptr : p->inv_scale, iq,
-                           p->storage, B, fb, nch, QM, p->K, s));
+                           p->storage, B, fb, nch, QM, p->K, col, s));
     p->launches += 1;
     *z_out = p->z;
     return DAS_OK;
@@ -735,9 +743,11 @@ int das_forward(das_plan_t *plan, const void *y_dev, void *x_dev, int batch, das
     if (plan->tuning.tensor_cores) return forward_tc(plan, y_dev, x_dev, batch, s);
     const int fb = choose_fb(plan, batch, MODE_FWD);
     const int nch = (batch + fb - 1) / fb;
+    const int col = col_layout(plan, fb);
     const void *z = nullptr;
-    if ((rc = stage_channels(plan, y_dev, batch, fb, nch, s, &z)) != DAS_OK) return rc;
+    if ((rc = stage_channels(plan, y_dev, batch, fb, nch, col, s, &z)) != DAS_OK) return rc;
     TileArgs A = tile_args(plan, batch, fb, z);
+    A.col = col;
     A.x = x_dev;
     const bool timed = plan->ev_used < (int)plan->ev_start.size();
     if (timed) DAS_CU(cudaEventRecord(plan->ev_start[plan->ev_used], s));
@@ -1011,9 +1021,11 @@ int das_grad_c(das_plan_t *plan, const void *y_dev, const void *gx_dev, double *
     if ((rc = prepare_if_dirty(plan, s)) != DAS_OK) return rc;
     const int fb = choose_fb(plan, batch, MODE_DC);
     const int nch = (batch + fb - 1) / fb;
+    const int col = col_layout(plan, fb);
     const void *z = nullptr;
-    if ((rc = stage_channels(plan, y_dev, batch, fb, nch, s, &z)) != DAS_OK) return rc;
+    if ((rc = stage_channels(plan, y_dev, batch, fb, nch, col, s, &z)) != DAS_OK) return rc;
     TileArgs A = tile_args(plan, batch, fb, z);
+    A.col = col;
     A.gx = gx_dev;
     A.partial = plan->partial;
     const long long np = n_tiles(plan->g) * nch;
@@ -1106,9 +1118,11 @@ extern "C" int das_grad_c_static(das_plan_t *plan, const void *y_dev, const void
     if ((rc = static_partials_address(plan->device, &partial)) != DAS_OK) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     if ((rc = prepare_if_dirty(plan, s)) != DAS_OK) return rc;
+    const int col = col_layout(plan, fb);
     const void *z = nullptr;
-    if ((rc = stage_channels(plan, y_dev, batch, fb, nch, s, &z)) != DAS_OK) return rc;
+    if ((rc = stage_channels(plan, y_dev, batch, fb, nch, col, s, &z)) != DAS_OK) return rc;
     TileArgs A = tile_args(plan, batch, fb, z);
+    A.col = col;
     A.gx = gx_dev;
     A.partial = partial;  // every slot 0..np-1 is written by its CTA before the reduction reads it
     DAS_CU(launch_tile(A, MODE_DC, is_iq(plan), DAS_STORE_F32, fb, nch, s));
@@ -1310,7 +1324,7 @@ extern "C" int das_batch_forward(das_batch_t *b, const void *const *y_dev, void 
             const int nch = (b->frames[i] + b->fb - 1) / b->fb;
             const long long l0 = p->launches;
             const void *z = nullptr;
-            rc = stage_channels(p, y_dev[i], b->frames[i], b->fb, nch, b->cap, &z);
+            rc = stage_channels(p, y_dev[i], b->frames[i], b->fb, nch, 0, b->cap, &z);
             kernels += (int)(p->launches - l0);
             P.plans[i] = tile_args(p, b->frames[i], b->fb, z);
             P.plans[i].x = x_dev[i];

@@ -18,6 +18,13 @@ bool tile_fb_supported(int mode, int iq, int store, int fb) {
     return fb == 1 || fb == 2 || fb == 4 || fb == 8 || fb == 12 || fb == 16 || fb == 20 || fb == 24;
 }
 
+bool tile_col_supported(int iq, int store, int fb) {
+    // bytes per sample; the same rule as ColShape in das_tile.cuh
+    const int sz = (iq ? 2 : 1) * (store == ST_F32 ? 4 : store == ST_E4M3 ? 1 : 2);
+    const int fg = (fb % 4 == 0 && (4 * sz) % 16 == 0) ? 4 : fb;
+    return fb >= 1 && (fb * sz) % 16 == 0 && (fg * sz) % 16 == 0;
+}
+
 cudaError_t launch_tile(const TileArgs &A, int mode, int iq, int store, int fb, int n_chunks, cudaStream_t s) {
     if (!tile_fb_supported(mode, iq, store, fb)) return cudaErrorInvalidValue;
     if (mode == MODE_COUNT || store == ST_F32) return launch_tile_f32(A, mode, iq, fb, n_chunks, s);

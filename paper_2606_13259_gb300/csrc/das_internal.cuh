@@ -80,6 +80,7 @@ struct TileArgs {
     int fb;        // frames per CTA chunk (= template FB) = samples per relayouted row
     int umax;      // rows per staged sample window (staged kernels); 0: rows come from global memory
     int w256;      // 1: 256-bit global sample loads where rows allow
+    int col;       // 1: z holds each (chunk, q, m) block in column order (LD_COL in das_tile.cuh)
     float win_lo;  // a * tile radius + margin: lower reach of a window below the tile reference (samples)
     double ad;     // fs / c, float64
     float a;       // fs / c, float32
@@ -133,6 +134,13 @@ cudaError_t launch_tile(const TileArgs &args, int mode, int iq, int store, int f
 cudaError_t launch_adjoint(const AdjArgs &args, int iq, cudaStream_t s);
 cudaError_t launch_reduce(const double *partial, long long n, double *out, cudaStream_t s);
 bool tile_fb_supported(int mode, int iq, int store, int fb);
+// Whether rows of fb samples can be read in column order (whole 16-byte
+// pieces per row and per register group of the tile kernels).
+bool tile_col_supported(int iq, int store, int fb);
+// Relayout of public channel data y[b][q][m][k] into the plan scratch
+// z[chunk][q][m][K rows of fb samples] (das_prep.cu); col: column order.
+cudaError_t launch_relayout(const void *y, void *z, const float2 *rot, const float *inv_scale, int iq, int store,
+                            int B, int fb, int nch, int QM, int K, int col, cudaStream_t s);
 // Rows of a staged window: every (voxel, element, transmit) of a tile falls in
 // [Tb + Rb + floor(rf + tmin - a R), + 4 a R + 3], R the tile radius.
 int window_rows(double a_R);

@@ -157,20 +157,32 @@ cudaError_t launch_scale(const void *y, float *scale, float *inv_scale, int iq, 
 // relayout
 // ---------------------------------------------------------------------------
 
+// Byte offset of byte `rb` of row k inside a (chunk, q, m) block of K rows of
+// RB bytes: row order (k * RB + rb), or column order (16-byte piece rb / 16 of
+// every row in one column of K pieces: (rb / 16) * K * 16 + k * 16 + rb % 16).
+__device__ __forceinline__ size_t row_byte(int k, int rb, int K, int RB, bool col) {
+    return col ? (size_t)(rb >> 4) * ((size_t)K * 16) + (size_t)k * 16 + (rb & 15) : (size_t)k * RB + rb;
+}
+
 // Batched: 32 frames x 32 samples per step through shared memory; reads are
 // contiguous along k, writes contiguous along the frames of a chunk.  The
-// output is chunk-major, z[c][qm][k][fb] holding frame b = c * fb + j, so the
-// rows one CTA of the tile kernels reads are contiguous.  For IQ data and an
-// even fb a row is stored pair-planar (re_0, re_1, im_0, im_1, re_2, ...), so
-// the kernels can update two frames with one packed float32 FMA.  Frames
-// B .. Bs-1 (Bs = chunks * fb) are zero.
+// output is chunk-major, z[c][qm][K rows of fb samples] holding frame
+// b = c * fb + j, so the rows one CTA of the tile kernels reads lie in one
+// block.  For IQ data and an even fb a row is stored pair-planar (re_0, re_1,
+// im_0, im_1, re_2, ...), so the kernels can update two frames with one packed
+// float32 FMA.  With `col` each block is stored in column order (row_byte).
+// Frames B .. Bs-1 (Bs = chunks * fb) are zero.
 template <bool IQ, int ST>
 __global__ void __launch_bounds__(256) relayout_kernel(const void *__restrict__ y_, void *__restrict__ z_,
                                                        const float2 *__restrict__ rot,
                                                        const float *__restrict__ inv_scale, int B, int fb, int Bs,
-                                                       int QM, int K) {
+                                                       int QM, int K, int col) {
     using OutC = typename StoreT<ST>::c;
     using OutR = typename StoreT<ST>::r;
+    constexpr int CB = (int)sizeof(OutR);          // bytes per component
+    constexpr int SB = IQ ? 2 * CB : CB;           // bytes per sample
+    unsigned char *zb = reinterpret_cast<unsigned char *>(z_);
+    const int RB = fb * SB;
     __shared__ float2 tile[32][33];
     const int k0 = blockIdx.x * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
@@ -195,21 +207,21 @@ __global__ void __launch_bounds__(256) relayout_kernel(const void *__restrict__ 
             if (k < K && b < Bs) {
                 float2 v = tile[tx][kl];
                 const int c = b / fb, j = b - c * fb;
-                const size_t o = (((size_t)c * QM + qm) * K + k) * (size_t)fb + j;
+                unsigned char *blk = zb + ((size_t)c * QM + qm) * (size_t)K * RB;
                 if (IQ) {
                     if (rot) v = cmul(v, rot[k]);
                     v.x *= s;
                     v.y *= s;
                     if (fb % 2 == 0) {
                         // pair-planar rows: re_{2p}, re_{2p+1}, im_{2p}, im_{2p+1}
-                        const size_t r = 2 * (o - j) + 4 * (j >> 1) + (j & 1);
-                        put(reinterpret_cast<OutR *>(z_) + r, v.x);
-                        put(reinterpret_cast<OutR *>(z_) + r + 2, v.y);
+                        const int rre = CB * (4 * (j >> 1) + (j & 1));
+                        put(reinterpret_cast<OutR *>(blk + row_byte(k, rre, K, RB, col)), v.x);
+                        put(reinterpret_cast<OutR *>(blk + row_byte(k, rre + 2 * CB, K, RB, col)), v.y);
                     } else {
-                        put(reinterpret_cast<OutC *>(z_) + o, v);
+                        put(reinterpret_cast<OutC *>(blk + row_byte(k, SB * j, K, RB, col)), v);
                     }
                 } else {
-                    put(reinterpret_cast<OutR *>(z_) + o, v.x * s);
+                    put(reinterpret_cast<OutR *>(blk + row_byte(k, CB * j, K, RB, col)), v.x * s);
                 }
             }
         }
@@ -242,32 +254,40 @@ __global__ void __launch_bounds__(256) convert1_kernel(const void *__restrict__ 
 }
 
 template <bool IQ, int ST>
-static void relayout_dispatch(const void *y, void *z, const float2 *rot, const float *inv_scale, int B, int fb,
-                              int nch, int QM, int K, cudaStream_t s) {
+static cudaError_t relayout_dispatch(const void *y, void *z, const float2 *rot, const float *inv_scale, int B,
+                                     int fb, int nch, int QM, int K, int col, cudaStream_t s) {
     const int Bs = fb * nch;
     if (Bs == 1) {
+        if (col) return cudaErrorInvalidValue;  // single-sample rows are never read in column order
+        int dev = 0, sms = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
         const size_t total = (size_t)QM * K;
-        const int blocks = (int)((total + 255) / 256 < 152 * 32 ? (total + 255) / 256 : 152 * 32);
+        const size_t cap = (size_t)sms * 32;
+        const int blocks = (int)((total + 255) / 256 < cap ? (total + 255) / 256 : cap);
         convert1_kernel<IQ, ST><<<blocks, 256, 0, s>>>(y, z, rot, inv_scale, QM, K);
     } else {
         dim3 grid((K + 31) / 32, QM < 65535 ? QM : 65535);
-        relayout_kernel<IQ, ST><<<grid, 256, 0, s>>>(y, z, rot, inv_scale, B, fb, Bs, QM, K);
+        relayout_kernel<IQ, ST><<<grid, 256, 0, s>>>(y, z, rot, inv_scale, B, fb, Bs, QM, K, col);
     }
+    return cudaSuccess;
 }
 
 cudaError_t launch_relayout(const void *y, void *z, const float2 *rot, const float *inv_scale, int iq, int store,
-                            int B, int fb, int nch, int QM, int K, cudaStream_t s) {
+                            int B, int fb, int nch, int QM, int K, int col, cudaStream_t s) {
+    cudaError_t e;
     if (iq) {
-        if (store == ST_F32) relayout_dispatch<true, ST_F32>(y, z, rot, inv_scale, B, fb, nch, QM, K, s);
-        else if (store == ST_F16) relayout_dispatch<true, ST_F16>(y, z, rot, inv_scale, B, fb, nch, QM, K, s);
-        else if (store == ST_BF16) relayout_dispatch<true, ST_BF16>(y, z, rot, inv_scale, B, fb, nch, QM, K, s);
-        else relayout_dispatch<true, ST_E4M3>(y, z, rot, inv_scale, B, fb, nch, QM, K, s);
+        if (store == ST_F32) e = relayout_dispatch<true, ST_F32>(y, z, rot, inv_scale, B, fb, nch, QM, K, col, s);
+        else if (store == ST_F16) e = relayout_dispatch<true, ST_F16>(y, z, rot, inv_scale, B, fb, nch, QM, K, col, s);
+        else if (store == ST_BF16) e = relayout_dispatch<true, ST_BF16>(y, z, rot, inv_scale, B, fb, nch, QM, K, col, s);
+        else e = relayout_dispatch<true, ST_E4M3>(y, z, rot, inv_scale, B, fb, nch, QM, K, col, s);
     } else {
-        if (store == ST_F32) relayout_dispatch<false, ST_F32>(y, z, rot, inv_scale, B, fb, nch, QM, K, s);
-        else if (store == ST_F16) relayout_dispatch<false, ST_F16>(y, z, rot, inv_scale, B, fb, nch, QM, K, s);
-        else relayout_dispatch<false, ST_BF16>(y, z, rot, inv_scale, B, fb, nch, QM, K, s);
+        if (store == ST_F32) e = relayout_dispatch<false, ST_F32>(y, z, rot, inv_scale, B, fb, nch, QM, K, col, s);
+        else if (store == ST_F16) e = relayout_dispatch<false, ST_F16>(y, z, rot, inv_scale, B, fb, nch, QM, K, col, s);
+        else e = relayout_dispatch<false, ST_BF16>(y, z, rot, inv_scale, B, fb, nch, QM, K, col, s);
     }
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

@@ -57,9 +57,6 @@ void tc_shape(int B, int max_bc, int &bc, int &nch, int &n);
 // Frames per chunk: 128 (N up to 256, one CTA per SM), or 112 when two CTAs
 // per SM are asked for (N <= 224 leaves room for the weight stages).
 inline int tc_max_frames(int ctas_per_sm) { return ctas_per_sm == 2 ? 112 : 128; }
-// y[b][qm][k] -> z[c][qm][k][fb] with b = c * fb + j; frames B .. nch*fb-1 are zero.
-cudaError_t launch_relayout(const void *y, void *z, const float2 *rot, const float *inv_scale, int iq, int store,
-                            int B, int fb, int nch, int QM, int K, cudaStream_t s);
 cudaError_t launch_scale(const void *y, float *scale, float *inv_scale, int iq, int store, int B, int QM, int K,
                          cudaStream_t s);
 

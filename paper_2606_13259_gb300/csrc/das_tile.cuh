@@ -95,6 +95,27 @@ template <int FB, bool IQ, int ST> struct FrameRow {
     }
 };
 
+// How the tile kernels read sample rows from global memory.
+//  LD_ROW  rows of FB samples stored contiguously (z[chunk][q][m][k][FB]),
+//          128-bit loads;
+//  LD_W256 the same rows with 256-bit loads;
+//  LD_COL  the same bytes in column order: every row is cut into 16-byte
+//          pieces and piece j of row k sits at j * (K * 16) + k * 16 inside
+//          its (chunk, q, m) block, so the pieces of consecutive rows are
+//          adjacent.  Lanes of a quarter-warp whose delays differ by a row or
+//          two then read from one 128-byte line, where the row order puts
+//          each distinct row in a line of its own (each line costs the L1 one
+//          data-return wavefront).
+enum LoadMode { LD_ROW = 0, LD_W256 = 1, LD_COL = 2 };
+
+// Frames per register group of the global-load path, and whether the column
+// order applies (rows and groups of whole 16-byte pieces).
+template <int FB, bool IQ, int ST> struct ColShape {
+    static constexpr int SZ = SampleSize<IQ, ST>::v;
+    static constexpr int FG = (FB % 4 == 0 && (4 * SZ) % 16 == 0) ? 4 : FB;
+    static constexpr bool ok = (FB * SZ) % 16 == 0 && (FG * SZ) % 16 == 0;
+};
+
 // 256-bit read-only global load (sm_100+), 32-byte aligned.
 __device__ __forceinline__ void ldg256(const void *p, uint32_t *w) {
     asm volatile("ld.global.nc.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
@@ -111,6 +132,18 @@ __device__ __forceinline__ void load_row(const unsigned char *p, uint32_t (&w)[F
         for (int i = 0; i < Row::NW / 8; ++i) ldg256(p + 32 * i, &w[8 * i]);
     } else {
         Row::load(p, w);
+    }
+}
+
+// FB samples of one row in column order: 16-byte piece i at p + i * cs.
+template <int FB, bool IQ, int ST>
+__device__ __forceinline__ void load_col(const unsigned char *p, size_t cs, uint32_t (&w)[FrameRow<FB, IQ, ST>::NW]) {
+    using Row = FrameRow<FB, IQ, ST>;
+    static_assert(!Row::HALFWORDS && Row::BYTES % 16 == 0, "column order needs whole 16-byte pieces");
+#pragma unroll
+    for (int i = 0; i < Row::NW / 4; ++i) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(p + i * cs));
+        w[4 * i] = v.x; w[4 * i + 1] = v.y; w[4 * i + 2] = v.z; w[4 * i + 3] = v.w;
     }
 }
 
@@ -231,7 +264,7 @@ template <int FB, int SZ = 4> struct TileOcc {
 // One (tile, frame chunk) of one plan with rows read from global memory;
 // `smem` is the CTA's dynamic shared memory (tile_smem_bytes).  Called by
 // tile_kernel (one launch per plan) and by the persistent batch kernel.
-template <int FB, bool IQ, int ST, int MODE, bool W256 = false>
+template <int FB, bool IQ, int ST, int MODE, int LD = LD_ROW>
 __device__ __forceinline__ void tile_body(const TileArgs &A, const long long tile, const int chunk,
                                           unsigned char *smem, const unsigned grid_x) {
     using Row = FrameRow<FB, IQ, ST>;
@@ -337,10 +370,11 @@ __device__ __forceinline__ void tile_body(const TileArgs &A, const long long til
             const float d = sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
             const float num = fmaf(2.f, fmaf(G.x, dx, fmaf(G.y, dy, G.z * dz)), dd);
             const float r = Nn.w + A.a * __fdividef(num, d + G.w);
-            // chunk-major rows: z[chunk][q][m][k][FB]
+            // chunk-major blocks of K rows: z[chunk][q][m][K rows of FB samples]
             const unsigned char *zrow = reinterpret_cast<const unsigned char *>(A.z) +
                                         (((size_t)chunk * Q * A.M + mm) * A.K) * (size_t)(FB * SZ);
             const size_t qstride = (size_t)A.M * A.K * (FB * SZ);
+            const size_t cs = (size_t)A.K * 16;  // LD_COL: bytes between the pieces of a row
 #pragma unroll 2
             for (int q = 0; q < Q; ++q) {
                 const float f = r + s_t[q * TILE_N + tid];
@@ -380,16 +414,25 @@ __device__ __forceinline__ void tile_body(const TileArgs &A, const long long til
                         c1r = s;
                     }
                 }
-                const unsigned char *p0 = zrow + q * qstride + (size_t)k * (FB * SZ);
-                const unsigned char *p1 = p0 + FB * SZ;
+                constexpr bool COL = LD == LD_COL;
+                constexpr int RSTEP = COL ? 16 : FB * SZ;  // bytes from row k to row k + 1
+                const unsigned char *p0 = zrow + q * qstride + (size_t)k * RSTEP;
+                const unsigned char *p1 = p0 + RSTEP;
                 // rows k and k+1 in groups of FG frames (fewer live registers)
-                constexpr int FG = (FB % 4 == 0 && (4 * SZ) % 16 == 0 && !W256) ? 4 : FB;
+                constexpr int FG = LD == LD_W256 ? FB : ColShape<FB, IQ, ST>::FG;
+                static_assert(!COL || ColShape<FB, IQ, ST>::ok, "column order needs whole 16-byte pieces");
                 using RowG = FrameRow<FG, IQ, ST>;
 #pragma unroll
                 for (int bg = 0; bg < FB; bg += FG) {
                     uint32_t w0[RowG::NW], w1[RowG::NW];
-                    load_row<FG, IQ, ST, W256>(p0 + bg * SZ, w0);
-                    load_row<FG, IQ, ST, W256>(p1 + bg * SZ, w1);
+                    if constexpr (COL) {
+                        const size_t off = (size_t)(bg * SZ / 16) * cs;
+                        load_col<FG, IQ, ST>(p0 + off, cs, w0);
+                        load_col<FG, IQ, ST>(p1 + off, cs, w1);
+                    } else {
+                        load_row<FG, IQ, ST, LD == LD_W256>(p0 + bg * SZ, w0);
+                        load_row<FG, IQ, ST, LD == LD_W256>(p1 + bg * SZ, w1);
+                    }
                     acc.template add<FG>(bg, w0, w1, c0r, c0i, c1r, c1i);
                 }
             }
@@ -438,10 +481,10 @@ __device__ __forceinline__ void tile_body(const TileArgs &A, const long long til
     }
 }
 
-template <int FB, bool IQ, int ST, int MODE, bool W256 = false>
+template <int FB, bool IQ, int ST, int MODE, int LD = LD_ROW>
 __global__ void __launch_bounds__(TILE_N, (TileOcc<FB, SampleSize<IQ, ST>::v>::v)) tile_kernel(const TileArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
-    tile_body<FB, IQ, ST, MODE, W256>(A, blockIdx.x, blockIdx.y, smem, gridDim.x);
+    tile_body<FB, IQ, ST, MODE, LD>(A, blockIdx.x, blockIdx.y, smem, gridDim.x);
 }
 
 inline size_t tile_smem_bytes(int Q, bool has_w) {
@@ -449,10 +492,10 @@ inline size_t tile_smem_bytes(int Q, bool has_w) {
            sizeof(int) * (2 * TILE_N + Q + 5);
 }
 
-template <int FB, bool IQ, int ST, int MODE, bool W256 = false>
+template <int FB, bool IQ, int ST, int MODE, int LD = LD_ROW>
 cudaError_t launch_tile_t(const TileArgs &A, int n_chunks, cudaStream_t s) {
     const size_t smem = tile_smem_bytes(A.Q, A.w_tx != nullptr);
-    auto kern = tile_kernel<FB, IQ, ST, MODE, W256>;
+    auto kern = tile_kernel<FB, IQ, ST, MODE, LD>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;

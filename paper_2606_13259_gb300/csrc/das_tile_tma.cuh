@@ -387,13 +387,17 @@ template <int FB, bool IQ, int ST, int MODE>
 cudaError_t launch_tile_best(const TileArgs &A, int n_chunks, cudaStream_t s) {
     constexpr int RB = FB * SampleSize<IQ, ST>::v;
     if constexpr (RB % 16 == 0) {
-        if (A.umax > 0 && tile_tma_smem_bytes(A.Q, A.w_tx != nullptr, A.umax, RB) <= 96 * 1024)
+        if (A.umax > 0 && !A.col && tile_tma_smem_bytes(A.Q, A.w_tx != nullptr, A.umax, RB) <= 96 * 1024)
             return launch_tile_tma_t<FB, IQ, ST, MODE>(A, n_chunks, s);
     }
     if constexpr (MODE == MODE_FWD && IQ && RB % 32 == 0) {
-        if (A.w256) return launch_tile_t<FB, IQ, ST, MODE, true>(A, n_chunks, s);
+        if (A.w256) return launch_tile_t<FB, IQ, ST, MODE, LD_W256>(A, n_chunks, s);
     }
-    return launch_tile_t<FB, IQ, ST, MODE>(A, n_chunks, s);
+    if constexpr (ColShape<FB, IQ, ST>::ok) {
+        if (A.col) return launch_tile_t<FB, IQ, ST, MODE, LD_COL>(A, n_chunks, s);
+    }
+    if (A.col) return cudaErrorInvalidValue;  // the data were laid out for a column read
+    return launch_tile_t<FB, IQ, ST, MODE, LD_ROW>(A, n_chunks, s);
 }
 
 }  // namespace das

@@ -6,7 +6,8 @@ import pytest
 import torch
 
 from paper_2606_13259_gb300 import synth as S
-from test_gpu_forward import RAGGED, ragged_scene, rel_l2
+from parity import assert_parity, rel_l2
+from test_gpu_forward import RAGGED, ragged_scene
 
 pytestmark = pytest.mark.gpu
 TOL_F32 = 1e-5
@@ -36,7 +37,7 @@ def test_adjoint_matches_oracle(das, oracle, case, B):
     plan = das.Plan.from_scene(sc, max_batch=B)
     y = plan.adjoint(x.cuda().reshape((B,) + plan.shape)).cpu().numpy()
     ref = oracle.adjoint(sc, x.numpy()).reshape(y.shape)
-    assert rel_l2(y, ref) <= TOL_F32
+    assert_parity(y, ref, TOL_F32, what=f"adjoint case {case}, {B} frames")
     plan.close()
 
 
@@ -49,7 +50,7 @@ def test_adjoint_and_grad_c_large_batches(das, oracle, B):
     y = S.random_channels(sc, B, seed=60 + B)
     plan = das.Plan.from_scene(sc, max_batch=B)
     ya = plan.adjoint(x.cuda().reshape((B,) + plan.shape)).cpu().numpy()
-    assert rel_l2(ya, oracle.adjoint(sc, x.numpy()).reshape(ya.shape)) <= TOL_F32
+    assert_parity(ya, oracle.adjoint(sc, x.numpy()).reshape(ya.shape), TOL_F32, what=f"adjoint {B} frames")
     got = float(plan.grad_c(y.cuda(), x.cuda().reshape((B,) + plan.shape)))
     ref = oracle.grad_c(sc, y.numpy(), x.numpy())
     assert abs(got - ref) <= 1e-4 * abs(ref)
@@ -66,7 +67,7 @@ def test_adjoint_small_and_dot_product(das, oracle, iq):
     plan = das.Plan.from_scene(sc, max_batch=B)
     ya = plan.adjoint(x.cuda().reshape((B,) + plan.shape))
     ref = oracle.adjoint(sc, x.numpy()).reshape(ya.shape)
-    assert rel_l2(ya.cpu().numpy(), ref) <= TOL_F32
+    assert_parity(ya.cpu().numpy(), ref, TOL_F32, what="adjoint small scene")
     Ay = plan.forward(y.cuda()).reshape(B, -1)
     lhs = torch.vdot(Ay.reshape(-1).to(torch.complex128), x.cuda().reshape(-1).to(torch.complex128))
     rhs = torch.vdot(y.cuda().reshape(-1).to(torch.complex128), ya.reshape(-1).to(torch.complex128))
@@ -85,7 +86,7 @@ def test_adjoint_diff_scale_sampled_rows(das, oracle):
     rows = np.array([0, 517, 1023 + 3 * 1024, 7 * 1024 + 500, 4 * 1024 + 255])
     ref = oracle.adjoint(sc, x.numpy(), rows=rows)
     got = y[:, torch.as_tensor(rows, device="cuda")].cpu().numpy()
-    assert rel_l2(got, ref) <= TOL_F32
+    assert_parity(got, ref, TOL_F32, what="adjoint sampled rows")
     plan.close()
 
 

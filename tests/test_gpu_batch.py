@@ -6,7 +6,8 @@ import pytest
 import torch
 
 from paper_2606_13259_gb300 import synth as S
-from test_gpu_forward import RAGGED, ragged_scene, rel_l2
+from parity import BAR, assert_parity, rel_l2
+from test_gpu_forward import RAGGED, ragged_scene
 
 pytestmark = pytest.mark.gpu
 
@@ -34,12 +35,12 @@ def test_batch_matches_oracle_and_replays(das, oracle, storage):
     ys = [S.random_channels(sc, f, seed=60 + i).cuda() for i, (sc, f) in enumerate(zip(scenes, frames))]
     plans = [das.Plan.from_scene(sc, storage=storage, max_batch=f) for sc, f in zip(scenes, frames)]
     batch = das.Batch(plans, frames)
-    tol = 1e-5 if storage == "f32" else 2e-2
+    tol = BAR[storage]
     for rep in range(2):  # capture, then replay
         outs = batch.forward(ys)
         for sc, y, x, p in zip(scenes, ys, outs, plans):
             ref = oracle.forward(sc, y.cpu().numpy())
-            assert rel_l2(x.reshape(x.shape[0], -1).cpu().numpy(), ref) <= tol
+            assert_parity(x.reshape(x.shape[0], -1).cpu().numpy(), ref, tol, what=f"{sc.name} {storage}")
             p.check()
     # single-plan calls give the same images
     for p, y, x in zip(plans, ys, outs):
@@ -89,9 +90,8 @@ def test_batched_workload_plans_sampled(das, oracle):
         vox = np.concatenate([rng.choice(sc.N, 48, replace=False), [sc.voxel_index(*q) for q in S.paper_points(sc)]])
         got = x.reshape(x.shape[0], -1)[:, torch.as_tensor(vox, device="cuda")].cpu().numpy()
         ref = oracle.forward(sc, y.cpu().numpy(), voxels=vox)
-        err = rel_l2(got, ref)
-        print(f"{sc.name}: f16 relative L2 {err:.2e}")
-        assert err <= 2e-3
+        e2, em = assert_parity(got, ref, BAR["f16"], what=sc.name)
+        print(f"{sc.name}: f16 relative L2 {e2:.2e}, element-wise {em:.2e}")
         p.check()
     batch.close()
     for p in plans:
@@ -120,7 +120,7 @@ def test_autotuner_choice_keeps_result(das, tmp_path, monkeypatch):
     # whichever kernel won, the plan's image stays within the 16-bit bar
     x = plans[0].forward(ys[0])
     plans[0].check()
-    assert rel_l2(x.cpu().numpy(), ref[0].cpu().numpy()) <= 2e-3
+    assert_parity(x.cpu().numpy(), ref[0].cpu().numpy(), BAR["f16"], what="tuned plan")
     batch.close()
     for p in plans:
         p.close()

@@ -1,8 +1,10 @@
 """Error of every storage form and forward path against the FP64 oracle:
 relative L2 and max-abs error (the largest |x - x_ref| over the largest
 |x_ref|, i.e. relative to the image peak), printed as one table row each and
-held to the bars of the forms (float32 1e-5, f16 2e-3, bf16 2e-2, E4M3 5e-2,
-relative L2); and the peak-position error at the point targets: the voxel of
+held to the bars of the forms (float32 1e-5, f16 and bf16 2e-3, E4M3 5e-2,
+relative L2, and the same fraction of the image peak element-wise; float32 at
+the paper workload's scale 5e-5 element-wise, tests/parity.py); and the
+peak-position error at the point targets: the voxel of
 the largest |x| near each target and its sub-voxel position (a parabola
 through the peak and its two neighbours along each axis), against the same
 on the oracle's image (the same voxel, positions within 0.1 voxel).
@@ -18,7 +20,7 @@ import torch
 from paper_2606_13259_gb300 import synth as S
 
 pytestmark = pytest.mark.gpu
-BAR = {"f32": 1e-5, "f16": 2e-3, "bf16": 2e-2, "e4m3": 5e-2}
+from parity import BAR, ELEM_F32_PAPER
 
 
 @pytest.fixture(scope="module")
@@ -109,7 +111,7 @@ def test_small_scene_errors(das, oracle, name, iq, storage, tc):
     shift, same, truth = peak_errors([x[:, b] for b in blocks], [ref[:, b] for b in blocks])
     print(f"\n| {name} | {'tensor cores' if tc else 'CUDA cores'} | {storage} | {rel:.2e} | {mx:.2e} | "
           f"{shift:.1e} | {truth:.2f} |")
-    assert rel <= BAR[storage]
+    assert rel <= BAR[storage] and mx <= BAR[storage]
     assert same and shift <= 0.1
 
 
@@ -132,5 +134,5 @@ def test_full_size_sampled_errors(das, oracle, workload, storage, tc):
                                      [ref[:, i * nb:(i + 1) * nb] for i in range(len(blocks))])
     print(f"\n| {workload} (sampled) | {'tensor cores' if tc else 'CUDA cores'} | {storage} | {rel:.2e} | {mx:.2e} | "
           f"{shift:.1e} | {truth:.2f} |")
-    assert rel <= BAR[storage]
+    assert rel <= BAR[storage] and mx <= (ELEM_F32_PAPER if storage == "f32" else BAR[storage])
     assert same and shift <= 0.1
