@@ -62,7 +62,7 @@ def parse_args():
                          "launch; table1: the paper's Table 1 configuration (B 128, Q 1, K 256)")
     ap.add_argument("--frames", type=int, default=20)
     ap.add_argument("--K", type=int, default=2048, help="samples per channel (all delays lie below 400)")
-    ap.add_argument("--storage", choices=["f32", "f16", "bf16", "e4m3"], default="f32")
+    ap.add_argument("--storage", choices=["f32", "f16", "bf16", "e4m3", "e5m2"], default="f32")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -628,7 +628,7 @@ def main():
     flops = active * F * 16.0          # 8 FMA per contributing (voxel, element, transmit, frame) term
     work = f"{active} contributing terms x {F} frames x 16 flop"
     achieved = flops / (kern_ms * 1e-3) / 1e12
-    bytes_store = {"f32": 8, "f16": 4, "bf16": 4, "e4m3": 2}[args.storage]
+    bytes_store = {"f32": 8, "f16": 4, "bf16": 4, "e4m3": 2, "e5m2": 2}[args.storage]
     alg_bytes = sc.Q * sc.M * sc.K * F * bytes_store + F * sc.N * 8
     if args.tensor_cores:
         roof = tensor_roofline(plan, items0, kern_n, kern_ms, args.storage, "tc_kernel_paper_iq", flops, work,

@@ -73,8 +73,10 @@ enum {
     DAS_STORE_F32 = 0,
     DAS_STORE_F16 = 1, /* half, with a float32 scale per (transmit, element) */
     DAS_STORE_BF16 = 2, /* bfloat16, with a float32 scale per (transmit, element) */
-    DAS_STORE_E4M3 = 3  /* 8-bit float E4M3 (IQ data only; the paper's future-work format), the largest
-                           component of each (transmit, element) scaled to 448 */
+    DAS_STORE_E4M3 = 3, /* 8-bit float E4M3 (IQ data only; 8-bit storage is the paper's future work,
+                           Sec. 6), the largest component of each (transmit, element) scaled to 448 */
+    DAS_STORE_E5M2 = 4  /* 8-bit float E5M2 (IQ data only; two mantissa bits, a wider exponent range),
+                           the largest component of each (transmit, element) scaled to 57344 */
 };
 
 /* Receive array (Sec. 2: receivers r_m, each with an origin and a direction). */
@@ -285,6 +287,19 @@ void das_batch_destroy(das_batch_t *batch);
  * met an item needing more sample windows than one work list holds (it
  * then left its outputs incomplete).  Clears the record. */
 int das_plan_check(das_plan_t *plan, das_stream_t stream);
+
+/* Test hook for the kernels' bounded waits (no counterpart in the paper:
+ * failure handling around Eq. 2).  wait_ns (0 .. 1e10; 0 restores the default
+ * of 1 s) limits every hand-off wait of the tensor-core pipeline, and the test
+ * wait below in the staged kernel; the waits that let copies and MMAs still in
+ * flight land before a CTA leaves keep their own 1 s limit.  probe = 1 makes
+ * the first CTA of the next launches wait once on a shared-memory barrier that
+ * nothing arrives on (the tensor-core kernel's MMA-issuing thread, or warp 1
+ * of the staged kernel), so that the wait runs out after wait_ns: the CTA
+ * records the failure in the plan's error word, drains, and leaves its part of
+ * the output unwritten, and das_plan_check reports DAS_ERR_TIMEOUT.  Applies
+ * to the calls issued after it; host only, synchronous, no allocation. */
+int das_plan_set_wait_test(das_plan_t *plan, long long wait_ns, int probe);
 
 /* Kernel timing for benchmarks.  With capacity > 0 the plan records a CUDA
  * event pair around the delay-and-sum kernel of each following das_forward

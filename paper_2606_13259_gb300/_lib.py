@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(HERE, "libdas_gb300.so")
 DAS_OK, DAS_ERR_INVALID_ARG, DAS_ERR_CUDA, DAS_ERR_OOM, DAS_ERR_UNSUPPORTED, DAS_ERR_TIMEOUT = range(6)
 DAS_TX_DIVERGING, DAS_TX_PLANE, DAS_TX_NONE = 0, 1, 2
 DAS_SAMPLE_F32, DAS_SAMPLE_C64 = 0, 1
-DAS_STORE_F32, DAS_STORE_F16, DAS_STORE_BF16, DAS_STORE_E4M3 = 0, 1, 2, 3
+DAS_STORE_F32, DAS_STORE_F16, DAS_STORE_BF16, DAS_STORE_E4M3, DAS_STORE_E5M2 = 0, 1, 2, 3, 4
 
 ERROR_NAMES = {DAS_ERR_INVALID_ARG: "invalid argument", DAS_ERR_CUDA: "CUDA error", DAS_ERR_OOM: "out of memory",
                DAS_ERR_UNSUPPORTED: "unsupported", DAS_ERR_TIMEOUT: "timeout"}
@@ -24,7 +24,8 @@ EXPORTS = ["das_plan_create", "das_plan_destroy", "das_plan_set_c", "das_plan_in
            "das_forward", "das_forward_host", "das_adjoint", "das_grad_c", "das_count_active",
            "das_plan_enable_timing", "das_plan_timing", "das_last_error", "das_version", "das_grad_c_static",
            "das_plan_check", "das_batch_create", "das_batch_forward", "das_batch_set_tuning", "das_batch_info",
-           "das_batch_destroy", "das_host_alloc", "das_host_free", "das_forward_host_many"]
+           "das_batch_destroy", "das_host_alloc", "das_host_free", "das_forward_host_many",
+           "das_plan_set_wait_test"]
 
 
 class Geometry(C.Structure):
@@ -109,6 +110,8 @@ def lib():
         L.das_batch_destroy.restype = None
         L.das_plan_check.argtypes = [vp, vp]
         L.das_plan_check.restype = i
+        L.das_plan_set_wait_test.argtypes = [vp, C.c_longlong, i]
+        L.das_plan_set_wait_test.restype = i
         L.das_plan_enable_timing.argtypes = [vp, i]
         L.das_plan_enable_timing.restype = i
         L.das_plan_timing.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int)]

@@ -93,6 +93,8 @@ struct das_plan {
     unsigned long long *tc_items = nullptr;  // MMA sub-items issued (tensor-core path)
     int tc_n = 0;              // MMA N of the last tensor-core call
     bool dirty = true;
+    unsigned long long wait_ns = 0;  // test hook: limit of the kernels' pipeline waits (0: 1 s)
+    int wait_probe = 0;              // test hook: one CTA waits on a barrier nothing arrives on
     das_tuning_t tuning{0, 0, 0, 0, 0};
     size_t bytes = 0;
     long long launches = 0;
@@ -147,7 +149,7 @@ int sample_bytes_public(const das_plan *p) { return is_iq(p) ? 8 : 4; }
 
 int sample_bytes_store(const das_plan *p) {
     const int comp = is_iq(p) ? 2 : 1;
-    return comp * (p->storage == DAS_STORE_F32 ? 4 : p->storage == DAS_STORE_E4M3 ? 1 : 2);
+    return comp * (p->storage == DAS_STORE_F32 ? 4 : (p->storage == DAS_STORE_E4M3 || p->storage == DAS_STORE_E5M2) ? 1 : 2);
 }
 
 const int FB_F32[] = {20, 16, 12, 8, 4, 2, 1};
@@ -248,6 +250,8 @@ TileArgs tile_args(const das_plan *p, int B, int fb, const void *z) {
     A.win_lo = (float)(aR + 1e-3);
     A.tx_tmin = p->tx_tmin;
     A.err = p->err;
+    A.wait_ns = p->wait_ns;
+    A.probe = p->wait_probe;
     A.inv_c = 1.0 / p->c;
     A.elem_pos = p->elem_pos;
     A.elem_nrm = p->elem_nrm;
@@ -368,6 +372,8 @@ int forward_tc(das_plan *p, const void *y, void *x, int B, cudaStream_t s) {
     A.ratio = p->ratio;
     A.smax = p->smax;
     A.err = p->err;
+    A.wait_ns = p->wait_ns;
+    A.probe = p->wait_probe;
     A.items = p->tc_items;
     A.x = reinterpret_cast<float2 *>(x);
     A.chain = p->tuning.tc_chain > 0 ? p->tuning.tc_chain
@@ -441,10 +447,11 @@ int das_plan_create(das_plan_t **out, const das_geometry_t *geometry, const das_
     if (options->n_samples < 2) return fail(DAS_ERR_INVALID_ARG, "n_samples must be >= 2");
     if (options->sample_type != DAS_SAMPLE_F32 && options->sample_type != DAS_SAMPLE_C64)
         return fail(DAS_ERR_INVALID_ARG, "unknown sample_type %d", options->sample_type);
-    if (options->storage < DAS_STORE_F32 || options->storage > DAS_STORE_E4M3)
+    if (options->storage < DAS_STORE_F32 || options->storage > DAS_STORE_E5M2)
         return fail(DAS_ERR_INVALID_ARG, "unknown storage %d", options->storage);
-    if (options->storage == DAS_STORE_E4M3 && options->sample_type != DAS_SAMPLE_C64)
-        return fail(DAS_ERR_UNSUPPORTED, "E4M3 storage is provided for IQ data only");
+    if ((options->storage == DAS_STORE_E4M3 || options->storage == DAS_STORE_E5M2) &&
+        options->sample_type != DAS_SAMPLE_C64)
+        return fail(DAS_ERR_UNSUPPORTED, "8-bit storage is provided for IQ data only");
     if (options->max_batch < 1) return fail(DAS_ERR_INVALID_ARG, "max_batch must be >= 1");
     if (options->sample_type == DAS_SAMPLE_F32 && f_demod != 0.0)
         return fail(DAS_ERR_INVALID_ARG, "real RF data (DAS_SAMPLE_F32) need f_demod = 0");
@@ -667,6 +674,15 @@ int das_plan_check(das_plan_t *plan, das_stream_t stream) {
         DAS_CU(cudaStreamSynchronize((cudaStream_t)stream));
         return fail(DAS_ERR_TIMEOUT, "a kernel gave up a bounded wait or lost a term (error word 0x%x)", flags);
     }
+    return DAS_OK;
+}
+
+int das_plan_set_wait_test(das_plan_t *plan, long long wait_ns, int probe) {
+    if (!plan) return fail(DAS_ERR_INVALID_ARG, "plan is NULL");
+    if (wait_ns < 0 || wait_ns > 10000000000LL) return fail(DAS_ERR_INVALID_ARG, "wait_ns must lie in 0 .. 1e10");
+    if (probe != 0 && probe != 1) return fail(DAS_ERR_INVALID_ARG, "probe must be 0 or 1");
+    plan->wait_ns = (unsigned long long)wait_ns;
+    plan->wait_probe = probe;
     return DAS_OK;
 }
 

@@ -51,6 +51,29 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return false;
 }
 
+// The same, also giving up once *flag is set (another warp of the CTA gave up).
+__device__ __forceinline__ bool mbar_wait_bounded_or(uint64_t *bar, uint32_t parity, const volatile int *flag) {
+    for (uint32_t i = 0; i < TMA_WAIT_LIMIT; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 63u) == 63u && *flag) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait bounded by wall time (ns); false when the limit ran out.
+__device__ __forceinline__ bool mbar_wait_ns(uint64_t *bar, uint32_t parity, uint64_t ns) {
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > ns) return false;
+    return true;
+}
+
 // Global -> shared bulk copy of `bytes` (multiple of 16, both ends 16-byte
 // aligned), completion reported to `bar` as transaction bytes.
 __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {

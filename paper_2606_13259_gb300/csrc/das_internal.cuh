@@ -39,7 +39,7 @@ constexpr int TILE_Z = 4;
 constexpr int TILE_N = TILE_X * TILE_Y * TILE_Z;  // 128 voxels, one per thread
 constexpr float APERTURE_MARGIN = 1e-6f;
 
-enum Store { ST_F32 = 0, ST_F16 = 1, ST_BF16 = 2, ST_E4M3 = 3 };
+enum Store { ST_F32 = 0, ST_F16 = 1, ST_BF16 = 2, ST_E4M3 = 3, ST_E5M2 = 4 };
 enum Mode { MODE_FWD = 0, MODE_DC = 1, MODE_COUNT = 2 };
 
 struct GridDesc {
@@ -98,6 +98,8 @@ struct TileArgs {
     const float *scale;        // [Q][M] storage scale, or null
     const void *z;             // channel data [chunk][Q][M][K][fb] (chunk-major)
     int *err;                  // device error flags (bit 0: a staged-copy wait timed out)
+    unsigned long long wait_ns;  // staged kernel, test hook: limit of the probe wait (0: 1 s)
+    int probe;                 // staged kernel, test hook: the first CTA waits on a barrier nothing arrives on
     void *x;                   // image [B][N] (MODE_FWD)
     const void *gx;            // cotangent [B][N] (MODE_DC)
     double *partial;           // per-CTA partial sums (MODE_DC, MODE_COUNT)

@@ -99,6 +99,10 @@ template <> struct StoreT<ST_F32> { using c = float2; using r = float; };
 template <> struct StoreT<ST_F16> { using c = __half2; using r = __half; };
 template <> struct StoreT<ST_BF16> { using c = __nv_bfloat162; using r = __nv_bfloat16; };
 template <> struct StoreT<ST_E4M3> { using c = __nv_fp8x2_storage_t; using r = __nv_fp8_storage_t; };
+// E5M2 bytes, as types of their own so that the conversion is chosen by type
+struct e5m2_t { __nv_fp8_storage_t v; };
+struct e5m2x2_t { __nv_fp8x2_storage_t v; };
+template <> struct StoreT<ST_E5M2> { using c = e5m2x2_t; using r = e5m2_t; };
 
 __device__ inline void put(float2 *p, float2 v) { *p = v; }
 __device__ inline void put(__half2 *p, float2 v) { *p = __floats2half2_rn(v.x, v.y); }
@@ -110,6 +114,8 @@ __device__ inline void put(__nv_fp8_storage_t *p, float v) { *p = __nv_cvt_float
 __device__ inline void put(__nv_fp8x2_storage_t *p, float2 v) {
     *p = __nv_cvt_float2_to_fp8x2(v, __NV_SATFINITE, __NV_E4M3);
 }
+__device__ inline void put(e5m2_t *p, float v) { p->v = __nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E5M2); }
+__device__ inline void put(e5m2x2_t *p, float2 v) { p->v = __nv_cvt_float2_to_fp8x2(v, __NV_SATFINITE, __NV_E5M2); }
 
 __device__ inline float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 
@@ -118,7 +124,7 @@ __device__ inline float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x
 // ---------------------------------------------------------------------------
 
 // The scale maps the largest component to `range` (1 for 16-bit storage, the
-// largest finite E4M3 value for 8-bit storage).
+// largest finite value of the format for 8-bit storage: 448 E4M3, 57344 E5M2).
 template <bool IQ>
 __global__ void __launch_bounds__(256) scale_kernel(const float *__restrict__ y, float *__restrict__ scale,
                                                     float *__restrict__ inv_scale, int B, int QM, int K,
@@ -147,7 +153,7 @@ __global__ void __launch_bounds__(256) scale_kernel(const float *__restrict__ y,
 
 cudaError_t launch_scale(const void *y, float *scale, float *inv_scale, int iq, int store, int B, int QM, int K,
                          cudaStream_t s) {
-    const float range = store == ST_E4M3 ? 448.f : 1.f;
+    const float range = store == ST_E4M3 ? 448.f : store == ST_E5M2 ? 57344.f : 1.f;
     if (iq) scale_kernel<true><<<QM, 256, 0, s>>>((const float *)y, scale, inv_scale, B, QM, K, range);
     else scale_kernel<false><<<QM, 256, 0, s>>>((const float *)y, scale, inv_scale, B, QM, K, range);
     return cudaGetLastError();
@@ -281,7 +287,8 @@ cudaError_t launch_relayout(const void *y, void *z, const float2 *rot, const flo
         if (store == ST_F32) e = relayout_dispatch<true, ST_F32>(y, z, rot, inv_scale, B, fb, nch, QM, K, col, s);
         else if (store == ST_F16) e = relayout_dispatch<true, ST_F16>(y, z, rot, inv_scale, B, fb, nch, QM, K, col, s);
         else if (store == ST_BF16) e = relayout_dispatch<true, ST_BF16>(y, z, rot, inv_scale, B, fb, nch, QM, K, col, s);
-        else e = relayout_dispatch<true, ST_E4M3>(y, z, rot, inv_scale, B, fb, nch, QM, K, col, s);
+        else if (store == ST_E4M3) e = relayout_dispatch<true, ST_E4M3>(y, z, rot, inv_scale, B, fb, nch, QM, K, col, s);
+        else e = relayout_dispatch<true, ST_E5M2>(y, z, rot, inv_scale, B, fb, nch, QM, K, col, s);
     } else {
         if (store == ST_F32) e = relayout_dispatch<false, ST_F32>(y, z, rot, inv_scale, B, fb, nch, QM, K, col, s);
         else if (store == ST_F16) e = relayout_dispatch<false, ST_F16>(y, z, rot, inv_scale, B, fb, nch, QM, K, col, s);

@@ -178,17 +178,15 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
     }
 }
 
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
 constexpr uint64_t TC_WAIT_NS = 1000000000ull;  // 1 s
 
-// Bounded wait (1 s of wall time); gives up early when another role of the
-// CTA, or another CTA, has recorded a timeout.
-__device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity, volatile uint32_t *abort_flag, int *err) {
+// Wait limit of the pipeline's hand-offs: the plan's test setting, else 1 s.
+__device__ __forceinline__ uint64_t tc_limit(const TcArgs &A) { return A.wait_ns ? A.wait_ns : TC_WAIT_NS; }
+
+// Bounded wait (`limit` ns of wall time); gives up early when another role of
+// the CTA, or another CTA, has recorded a timeout.
+__device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity, volatile uint32_t *abort_flag, int *err,
+                                        uint64_t limit) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     for (uint32_t i = 1;; ++i) {
@@ -198,7 +196,7 @@ __device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity, volatile
                 *abort_flag = 1u;
                 return false;
             }
-            if (global_ns() - t0 > TC_WAIT_NS) break;
+            if (global_ns() - t0 > limit) break;
         }
     }
     atomicOr(err, 4);
@@ -217,13 +215,14 @@ __device__ __forceinline__ void mbar_arrive_if(uint64_t *bar, bool p) {
 
 // Slow path of a whole warp's wait (the first try failed): every lane takes
 // the same decisions, so the warp stays converged.
-__device__ __noinline__ bool tc_wait_warp(uint64_t *bar, uint32_t parity, volatile uint32_t *abort_flag, int *err) {
+__device__ __noinline__ bool tc_wait_warp(uint64_t *bar, uint32_t parity, volatile uint32_t *abort_flag, int *err,
+                                          uint64_t limit) {
     const uint64_t t0 = global_ns();
     for (uint32_t i = 1;; ++i) {
         if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
         if ((i & 63u) == 0u) {
             const bool give_up = __any_sync(0xffffffffu, *abort_flag != 0u || (*(volatile int *)err & 4) != 0 ||
-                                                             global_ns() - t0 > TC_WAIT_NS);
+                                                             global_ns() - t0 > limit);
             if (give_up) break;
         }
     }
@@ -365,6 +364,7 @@ __global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_co
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L.bars);
     uint64_t *fullB = bars, *emptyB = bars + TC_MAX_SB, *fullA = bars + 2 * TC_MAX_SB, *emptyA = fullA + TC_MAX_SA;
     uint64_t *accFull = emptyA + TC_MAX_SA;
+    uint64_t *probe = accFull + 1;  // test hook: a barrier nothing arrives on
     uint32_t *misc = reinterpret_cast<uint32_t *>(smem + L.misc);
     volatile uint32_t *s_abort = misc + MW_ABORT;
     int2 *s_list = reinterpret_cast<int2 *>(smem + L.list);  // (window row, j | q << 9)
@@ -400,6 +400,7 @@ __global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_co
             mbar_init(&emptyA[s], 1);
         }
         mbar_init(accFull, 1);
+        mbar_init(probe, 1);
         misc[MW_ABORT] = (*(volatile int *)A.err & 4) ? 1u : 0u;  // another CTA gave up: leave at once
         misc[MW_ISSUED] = 0u;
         mbar_init_fence();
@@ -658,7 +659,7 @@ __global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_co
                     mbar_arrive_if(&fullA[pend_sa], pending && lane == 0);
                     const uint32_t sa = gi & (sa_n - 1u), use = gi >> sa_shift;
                     const bool ready = __all_sync(0xffffffffu, use == 0 || mbar_try_wait(&emptyA[sa], (use - 1) & 1u));
-                    if (!ready && !tc_wait_warp(&emptyA[sa], (use - 1) & 1u, s_abort, A.err)) {
+                    if (!ready && !tc_wait_warp(&emptyA[sa], (use - 1) & 1u, s_abort, A.err, tc_limit(A))) {
                         pending = false;
                         stop = true;
                         break;
@@ -682,7 +683,7 @@ __global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_co
                         const uint32_t gi = base + (uint32_t)e;
                         const int2 ent = s_list[e];
                         const int j = ent.y & 511, q = (ent.y >> 9) & 127;
-                        if (b_pass > 0 && !tc_wait(&emptyB[b_slot], (b_pass - 1) & 1u, s_abort, A.err)) {
+                        if (b_pass > 0 && !tc_wait(&emptyB[b_slot], (b_pass - 1) & 1u, s_abort, A.err, tc_limit(A))) {
                             stop = true;
                             break;
                         }
@@ -703,11 +704,16 @@ __global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_co
                     const uint32_t idesc = tc_idesc(n, BF16);
                     const uint64_t bdesc0 = smem_desc(smem_addr(sB), 128, 512);
                     uint32_t done = 0;
+                    // test hook (das_plan_set_wait_test): the first CTA's first
+                    // wait is on a barrier nothing arrives on, so it runs out
+                    if (A.probe && blockIdx.x == 0 && blockIdx.y == 0 && base == 0 && n_list > 0 &&
+                        !tc_wait(probe, 0u, s_abort, A.err, tc_limit(A)))
+                        stop = true;
                     for (int e = 0; e < n_list && !stop; ++e) {
                         const uint32_t gi = base + (uint32_t)e;
                         const uint32_t sa = gi & (sa_n - 1u), slot = b_slot;
-                        if (!tc_wait(&fullA[sa], (gi >> sa_shift) & 1u, s_abort, A.err) ||
-                            !tc_wait(&fullB[slot], b_pass & 1u, s_abort, A.err)) {
+                        if (!tc_wait(&fullA[sa], (gi >> sa_shift) & 1u, s_abort, A.err, tc_limit(A)) ||
+                            !tc_wait(&fullB[slot], b_pass & 1u, s_abort, A.err, tc_limit(A))) {
                             stop = true;
                             break;
                         }

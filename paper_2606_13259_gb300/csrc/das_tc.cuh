@@ -40,6 +40,8 @@ struct TcArgs {
     const float *ratio;   // [Q][M] weight factor sqrt(scale / largest scale)
     const float *smax;    // the largest storage scale
     int *err;             // bit 2: a wait timed out; bit 3: an item needed more windows than a list holds
+    unsigned long long wait_ns;  // limit of the pipeline waits (0: 1 s)
+    int probe;            // test hook: the first CTA waits on a barrier nothing arrives on
     unsigned long long *items;  // running count of MMA sub-items (128 x n x 32 each)
     float2 *x;            // image [B][N]
 };

@@ -32,10 +32,15 @@ template <> struct SampleSize<false, ST_F16> { static constexpr int v = 2; };
 template <> struct SampleSize<false, ST_BF16> { static constexpr int v = 2; };
 template <> struct SampleSize<true, ST_E4M3> { static constexpr int v = 2; };
 template <> struct SampleSize<false, ST_E4M3> { static constexpr int v = 1; };
+template <> struct SampleSize<true, ST_E5M2> { static constexpr int v = 2; };
+template <> struct SampleSize<false, ST_E5M2> { static constexpr int v = 1; };
 
-// Two E4M3 bytes (low byte first) as two floats.
-__device__ __forceinline__ float2 e4m3x2_to_float2(uint32_t bits16) {
-    const __half2_raw h = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(bits16 & 0xffffu), __NV_E4M3);
+// Two 8-bit floats (E4M3 or E5M2, low byte first) as two floats.
+template <int ST>
+__device__ __forceinline__ float2 fp8x2_to_float2(uint32_t bits16) {
+    static_assert(ST == ST_E4M3 || ST == ST_E5M2, "8-bit storage formats");
+    const __half2_raw h =
+        __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(bits16 & 0xffffu), ST == ST_E4M3 ? __NV_E4M3 : __NV_E5M2);
     return __half22float2(*reinterpret_cast<const __half2 *>(&h));
 }
 
@@ -81,9 +86,9 @@ template <int FB, bool IQ, int ST> struct FrameRow {
             __nv_bfloat162 h;
             *reinterpret_cast<uint32_t *>(&h) = w[b];
             return __bfloat1622float2(h);
-        } else if constexpr (IQ && ST == ST_E4M3) {
+        } else if constexpr (IQ && (ST == ST_E4M3 || ST == ST_E5M2)) {
             const uint32_t bits = HALFWORDS ? w[b] : (w[b >> 1] >> (16 * (b & 1)));
-            return e4m3x2_to_float2(bits);
+            return fp8x2_to_float2<ST>(bits);
         } else if constexpr (!IQ && ST == ST_F32) {
             return make_float2(__uint_as_float(w[b]), 0.f);
         } else {
@@ -183,9 +188,9 @@ template <int FB, bool IQ, int ST> struct FrameAcc {
             *reinterpret_cast<uint32_t *>(&b) = w[2 * p + 1];
             re = __bfloat1622float2(a);
             im = __bfloat1622float2(b);
-        } else if constexpr (IQ && ST == ST_E4M3) {
-            re = e4m3x2_to_float2(w[p]);        // bytes re_2p, re_2p+1
-            im = e4m3x2_to_float2(w[p] >> 16);  // bytes im_2p, im_2p+1
+        } else if constexpr (IQ && (ST == ST_E4M3 || ST == ST_E5M2)) {
+            re = fp8x2_to_float2<ST>(w[p]);        // bytes re_2p, re_2p+1
+            im = fp8x2_to_float2<ST>(w[p] >> 16);  // bytes im_2p, im_2p+1
         } else if constexpr (ST == ST_F32) {
             re = make_float2(__uint_as_float(w[2 * p]), __uint_as_float(w[2 * p + 1]));
         } else if constexpr (ST == ST_F16) {

@@ -59,7 +59,8 @@ __device__ __forceinline__ bool tile_tma_body(const TileArgs &A, const long long
     unsigned char *stages = smem;                                                        // [S][umax][RB]
     uint64_t *mbar = reinterpret_cast<uint64_t *>(stages + (size_t)TMA_STAGES * umax * RB);  // [S] full
     uint64_t *ebar = mbar + TMA_STAGES;                                                  // [S] empty
-    int2 *s_win = reinterpret_cast<int2 *>(ebar + TMA_STAGES);                          // [S] (first row, rows)
+    uint64_t *pbar = ebar + TMA_STAGES;                                                  // [2] test hook, pad
+    int2 *s_win = reinterpret_cast<int2 *>(pbar + 2);                                   // [S] (first row, rows)
     float4 *s_eg = reinterpret_cast<float4 *>(s_win + TMA_STAGES + (TMA_STAGES & 1));  // [128]
     float4 *s_en = s_eg + TILE_N;                                                        // [128]
     float *s_t = reinterpret_cast<float *>(s_en + TILE_N);                              // [Q][128]
@@ -106,6 +107,7 @@ __device__ __forceinline__ bool tile_tma_body(const TileArgs &A, const long long
             mbar_init(&mbar[s], 1);               // completes when the copy has landed
             mbar_init(&ebar[s], TILE_N / 32);     // completes when every warp is done with the stage
         }
+        mbar_init(pbar, 1);                       // nothing arrives on it (test hook)
         mbar_init_fence();
         *s_abort = 0;
     }
@@ -121,7 +123,7 @@ __device__ __forceinline__ bool tile_tma_body(const TileArgs &A, const long long
         const int j = i / Q, q = i - j * Q;
         const long long gi = g0 + i;
         if (gi >= TMA_STAGES &&
-            !mbar_wait_bounded(&ebar[gi % TMA_STAGES], (uint32_t)(((gi / TMA_STAGES) - 1) & 1)))
+            !mbar_wait_bounded_or(&ebar[gi % TMA_STAGES], (uint32_t)(((gi / TMA_STAGES) - 1) & 1), s_abort))
             return false;
         uint64_t *bar = &mbar[gi % TMA_STAGES];
         int ks, cnt;
@@ -219,7 +221,11 @@ __device__ __forceinline__ bool tile_tma_body(const TileArgs &A, const long long
             const long long gi = g0 + i;
             const int st = (int)(gi % TMA_STAGES);
             if (*abort_flag) break;  // warp-uniform: one shared word, read by the whole warp
-            const bool timed_out = !mbar_wait_bounded(&mbar[st], (uint32_t)((gi / TMA_STAGES) & 1));
+            // test hook (das_plan_set_wait_test): warp 1 of the first CTA waits
+            // on a barrier nothing arrives on for its first item, so it runs out
+            const bool probe = A.probe && tile == 0 && chunk == 0 && gi == 0 && warp == 1;
+            const bool timed_out = probe ? !mbar_wait_ns(pbar, 0u, A.wait_ns ? A.wait_ns : 1000000000ull)
+                                         : !mbar_wait_bounded(&mbar[st], (uint32_t)((gi / TMA_STAGES) & 1));
             if (__any_sync(0xffffffffu, timed_out)) {
                 if (lane == 0) atomicOr(A.err, 1);
                 *abort_flag = 1;
@@ -362,7 +368,7 @@ __global__ void __launch_bounds__(TILE_N, TmaOcc<FB>::v) tile_tma_kernel(const T
 }
 
 inline size_t tile_tma_smem_bytes(int Q, bool has_w, int umax, int rb) {
-    return (size_t)TMA_STAGES * umax * rb + sizeof(uint64_t) * 2 * TMA_STAGES +
+    return (size_t)TMA_STAGES * umax * rb + sizeof(uint64_t) * (2 * TMA_STAGES + 2) +
            sizeof(int2) * (TMA_STAGES + (TMA_STAGES & 1)) + sizeof(float4) * 2 * TILE_N +
            sizeof(float) * ((size_t)Q * TILE_N * (has_w ? 2 : 1) + Q) + sizeof(int) * (2 * TILE_N + Q + 5);
 }

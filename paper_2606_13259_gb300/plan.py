@@ -14,7 +14,8 @@ import torch
 
 from . import _lib as L
 
-STORAGE = {"f32": L.DAS_STORE_F32, "f16": L.DAS_STORE_F16, "bf16": L.DAS_STORE_BF16, "e4m3": L.DAS_STORE_E4M3}
+STORAGE = {"f32": L.DAS_STORE_F32, "f16": L.DAS_STORE_F16, "bf16": L.DAS_STORE_BF16, "e4m3": L.DAS_STORE_E4M3,
+           "e5m2": L.DAS_STORE_E5M2}
 
 
 def _stream(stream: Optional[torch.cuda.Stream]) -> C.c_void_p:
@@ -135,6 +136,12 @@ class Plan:
     def check(self, stream=None) -> None:
         """Wait for the stream; raise if a kernel recorded a failure (a bounded wait that expired)."""
         L.check(self._lib.das_plan_check(self._h, _stream(stream)))
+
+    def set_wait_test(self, wait_ns: int = 0, probe: bool = False) -> None:
+        """Test hook of the kernels' bounded waits (das_plan_set_wait_test):
+        the limit of the pipeline waits in ns (0: the default, 1 s) and whether
+        one CTA waits on a barrier nothing arrives on."""
+        L.check(self._lib.das_plan_set_wait_test(self._h, int(wait_ns), 1 if probe else 0))
 
     def enable_timing(self, capacity: int) -> None:
         """Record CUDA events around the DAS kernel of the next `capacity` forward calls."""

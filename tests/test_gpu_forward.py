@@ -138,9 +138,9 @@ def test_term_count_is_exact(das, oracle, name):
 
 
 @pytest.mark.parametrize("storage,tol,iq", [("f16", 2e-3, False), ("f16", 2e-3, True), ("bf16", 2e-3, False),
-                                            ("bf16", 2e-3, True), ("e4m3", 5e-2, True)])
+                                            ("bf16", 2e-3, True), ("e4m3", 5e-2, True), ("e5m2", 1e-1, True)])
 def test_16bit_storage(das, oracle, storage, tol, iq):
-    """16-bit (and 8-bit E4M3) storage with a float32 scale per (transmit,
+    """16-bit (and 8-bit E4M3 / E5M2) storage with a float32 scale per (transmit,
     element), float32 interpolation and sums."""
     sc = S.scene_small_iq() if iq else S.scene_small()
     y = S.frames(sc, 2, seed=1, n_speckle=2000, points=S.SMALL_POINTS, noise_db=30.0)

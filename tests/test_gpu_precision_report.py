@@ -98,7 +98,8 @@ def run(das, sc, y, storage, tc, voxels=None):
 
 CASES = [("small RF", False, "f32", False), ("small RF", False, "f16", False), ("small RF", False, "bf16", False),
          ("small IQ", True, "f32", False), ("small IQ", True, "f16", False), ("small IQ", True, "bf16", False),
-         ("small IQ", True, "e4m3", False), ("small IQ", True, "f16", True), ("small IQ", True, "bf16", True)]
+         ("small IQ", True, "e4m3", False), ("small IQ", True, "e5m2", False), ("small IQ", True, "f16", True),
+         ("small IQ", True, "bf16", True)]
 
 
 @pytest.mark.parametrize("name,iq,storage,tc", CASES)
