@@ -69,6 +69,9 @@ def parse_args():
     ap.add_argument("--staging", action="store_true", help="stage sample windows in shared memory (bulk copies)")
     ap.add_argument("--load-width", type=int, default=0, choices=[0, 128, 256], help="bits per lane of each load")
     ap.add_argument("--fb", type=int, default=0, help="frames per thread (0: automatic)")
+    ap.add_argument("--adj-rows", type=int, default=0, help="sample rows per adjoint CTA (0: automatic)")
+    ap.add_argument("--vpt", type=int, default=0, choices=[0, 1, 2],
+                    help="voxels per thread of the float32 IQ kernel (0: automatic = 1)")
     ap.add_argument("--tensor-cores", action="store_true",
                     help="forward pass as the tcgen05 tile contraction (f16 / bf16 storage)")
     ap.add_argument("--ctas", type=int, default=0, help="CTAs per SM of the tensor-core kernel (0: automatic)")
@@ -110,8 +113,9 @@ def measured_peaks():
 def apply_tuning(plan, args) -> None:
     if args.tensor_cores:
         plan.set_tuning(tensor_cores=True, ctas_per_sm=args.ctas, tc_chain=args.tc_chain)
-    elif args.staging or args.fb or args.load_width:
-        plan.set_tuning(frames_per_thread=args.fb, staging=args.staging, load_width=args.load_width)
+    elif args.staging or args.fb or args.load_width or args.vpt:
+        plan.set_tuning(frames_per_thread=args.fb, staging=args.staging, load_width=args.load_width,
+                        voxels_per_thread=args.vpt)
 
 
 def tensor_roofline(plan, items0: int, launches: int, kern_ms: float, storage: str, profile: str,
@@ -143,6 +147,7 @@ def tensor_roofline(plan, items0: int, launches: int, kern_ms: float, storage: s
 
 
 TILE_SOURCES = ("das_tile.cuh", "das_tile_tma.cuh", "das_tile_f32.cu", "das_internal.cuh")
+PAIR_SOURCES = ("das_tile_pair.cuh", "das_tile_pair.cu", "das_tile.cuh", "das_internal.cuh")
 TC_SOURCES = ("das_tc.cu", "das_tc.cuh", "das_async.cuh", "das_internal.cuh")
 
 
@@ -464,6 +469,8 @@ def run_diff(args):
     y = S.frames(sc, 1, seed=5, n_speckle=20000, points=S.paper_points(sc), c=1540.0, device="cuda")
     g = S.random_image(sc, 1, seed=12).cuda().reshape((1, sc.nz, sc.ny, sc.nx))
     plan = Plan.from_scene(sc)
+    if args.adj_rows:
+        plan.set_tuning(adjoint_rows=args.adj_rows)
     x = torch.empty((1,) + plan.shape, dtype=torch.complex64, device="cuda")
     ya = torch.empty_like(y)
     dc = torch.empty((), dtype=torch.float64, device="cuda")
@@ -495,7 +502,8 @@ def run_diff(args):
         "metric": "differentiation steps/s (forward + adjoint + dL/dc) at 96^3 voxels x 1024 elements x 8 transmits",
         "value": 1e3 / step, "unit": "steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic", "config": {"workload": sc.name, "frames": 1, "scene": sc.describe()},
+        "data": "synthetic", "config": {"workload": sc.name, "frames": 1, "scene": sc.describe(),
+                                        "adjoint_rows": args.adj_rows or "auto"},
         "ms": {"forward": t_fwd, "adjoint": t_adj, "grad_c": t_dc},
         "terms_per_ms": {"forward": active / t_fwd, "adjoint": active / t_adj, "grad_c": active / t_dc},
         "clocks": clocks,
@@ -636,9 +644,15 @@ def main():
         roof.update({"hbm_algorithmic_gbs": alg_bytes / (kern_ms * 1e-3) / 1e9, "sm_count": sms})
     else:
         roof = None
+    # --vpt 2 runs the two-voxels-per-thread kernel (das_tile_pair.cuh)
+    pair = (args.storage == "f32" and not args.tensor_cores and args.vpt == 2 and not args.staging
+            and not args.load_width)
     roof = roof or {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-            "frac": achieved / fp32_peak, "traffic": profiled_traffic(args.storage),
-            "kernel": "tile_kernel (forward DAS)", "kernel_ms": kern_ms,
+            "frac": achieved / fp32_peak,
+            "traffic": profiled_traffic(args.storage, "pair_kernel_paper_iq", PAIR_SOURCES) if pair
+            else profiled_traffic(args.storage),
+            "kernel": "pair_kernel (forward DAS, two voxels per thread)" if pair else "tile_kernel (forward DAS)",
+            "kernel_ms": kern_ms,
             "peak_source": f"{sms} SMs (device attribute) x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
                            f"({peak_src} max SM clock)",
             "hbm_algorithmic_gbs": alg_bytes / (kern_ms * 1e-3) / 1e9,
@@ -656,6 +670,7 @@ def main():
                    "l2": f"inputs {y.numel() * 8 / 1e9:.1f} GB > 129 MB L2, no flush", "per_rank_frames": F,
                    "staging": args.staging, "load_width": args.load_width or 128,
                    "frames_per_thread": args.fb or "auto", "tensor_cores": bool(args.tensor_cores),
+                   "voxels_per_thread": args.vpt or "auto",
                    **({"tc_chain": args.tc_chain or "auto"} if args.tensor_cores else {})},
         "accumulations_per_s": world * F * sc.N * sc.M * sc.Q / (ms * 1e-3),
         "accumulations_note": "accumulations_per_s counts the dense N x M x Q terms per volume (the paper's "

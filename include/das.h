@@ -153,6 +153,11 @@ typedef struct {
                               bias proportional to the chain rather than to all terms
                               (0: automatic, 1024 for plans of 4 or more transmits and one
                               chain per tile otherwise; -1: one chain per tile) */
+    int voxels_per_thread; /* forward kernel for float32 IQ data in column order: 2 gives each
+                              thread two voxels next to each other along x, which load three sample
+                              rows for their four taps; 0 (default) or 1: one voxel per thread */
+    int adjoint_rows;      /* das_adjoint: sample rows per CTA band (0: automatic); each CTA
+                              accumulates one band of one element's rows in shared memory */
 } das_tuning_t;
 
 /* Build a plan (Sec. 2 problem statement: grid, receivers, observations, c).

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libdas_gb300.so")
 
-SOURCES = ["das_tile_f32.cu", "das_tile_f16.cu", "das_tile_bf16.cu", "das_tile_e4m3.cu", "das_batch.cu", "das_tc.cu", "das_adjoint.cu",
+SOURCES = ["das_tile_pair.cu", "das_tile_f32.cu", "das_tile_f16.cu", "das_tile_bf16.cu", "das_tile_e4m3.cu", "das_batch.cu", "das_tc.cu", "das_adjoint.cu",
            "das_prep.cu", "das_dispatch.cu", "das_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -4,11 +4,16 @@
 // Each forward term reads two samples, w e^{i theta tau} ((1 - a) y[k] + a y[k+1]);
 // its adjoint sends conj(w e^{i theta tau}) (1 - a) x_n to y[k] and
 // conj(w e^{i theta tau}) a x_n to y[k+1].  The kernel is element-major: one
-// CTA owns the channel rows (q, m) of one element m for a chunk of transmits
-// and frames, accumulates them in shared memory while it visits every voxel
-// tile that can see the element, and writes each row once, in the public
-// layout y[b][q][m][k].  No global atomics; every output value is written by
-// exactly one CTA, zeros included.
+// CTA owns one band of `rows` samples of the channel rows (q, m) of one
+// element m, for a chunk of transmits and frames.  It accumulates the band in
+// shared memory while it visits every voxel tile that can see the element and
+// whose delays can reach the band (the tile's transmit row span from the
+// prepare kernel, widened by the receive offset bound), and writes the band
+// once, in the public layout y[b][q][m][k].  Most bands of a long record hold
+// no echo and are written as zeros at once; the others split an element's
+// work into pieces of similar size, so the grid is many short, balanced CTAs.
+// No global atomics; every output value is written by exactly one CTA, zeros
+// included.
 //
 // Delays use the same split as the forward kernels (float64 reference to the
 // tile centre, float32 offsets; see das_internal.cuh).
@@ -38,17 +43,20 @@ __global__ void __launch_bounds__(ADJ_THREADS, 2) adjoint_kernel(const AdjArgs A
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int C = IQ ? 2 : 1;
     const int m = blockIdx.x;
-    const int q0 = blockIdx.y * A.qc;
+    const int band = blockIdx.y % A.n_bands;
+    const int q0 = (blockIdx.y / A.n_bands) * A.qc;
     const int nq = min(A.qc, A.Q - q0);
     const int b0 = blockIdx.z * FB;
     const int K = A.K;
-    float *acc = reinterpret_cast<float *>(smem);                             // [qc][K][FB][C]
-    AdjTileRec *recs = reinterpret_cast<AdjTileRec *>(acc + (size_t)A.qc * K * FB * C);  // [ADJ_THREADS]
-    int *s_cnt = reinterpret_cast<int *>(recs + ADJ_THREADS);                 // [ADJ_THREADS / 32]
+    const int L = A.rows;
+    const int R0 = band * L, R1 = min(R0 + L, K);  // rows of this CTA
+    float *acc = reinterpret_cast<float *>(smem);                             // [qc][L][FB][C]
+    AdjTileRec *recs = reinterpret_cast<AdjTileRec *>(acc + (size_t)A.qc * L * FB * C);  // [2 ADJ_THREADS]
+    int *s_cnt = reinterpret_cast<int *>(recs + 2 * ADJ_THREADS);             // [ADJ_THREADS / 32]
 
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
-    for (int i = tid; i < A.qc * K * FB * C; i += ADJ_THREADS) acc[i] = 0.f;
+    for (int i = tid; i < A.qc * L * FB * C; i += ADJ_THREADS) acc[i] = 0.f;
 
     const GridDesc &g = A.g;
     const double rx = A.elem_pos[3 * m], ry = A.elem_pos[3 * m + 1], rz = A.elem_pos[3 * m + 2];
@@ -63,10 +71,16 @@ __global__ void __launch_bounds__(ADJ_THREADS, 2) adjoint_kernel(const AdjArgs A
     const float dy = (float)(g.sy * (ly - 0.5 * (TILE_Y - 1)));
     const float dz = (float)(g.sz * (lz - 0.5 * (TILE_Z - 1)));
 
+    // Candidate tiles are gathered over scan passes of ADJ_THREADS tiles into a
+    // buffer of 2 ADJ_THREADS records and processed once at least ADJ_THREADS
+    // are waiting (or the scan is over), so that every processing round gives
+    // each of the 32 tile slots a dozen tiles or more to balance.
+    int nbuf = 0;  // records waiting in the buffer (the same value in every thread)
     for (long long t0 = 0; t0 < ntiles; t0 += ADJ_THREADS) {
-        __syncthreads();  // records of the previous pass are no longer read (and acc is zeroed)
-        // float64 reference delay of element m to the tile centre, and a
-        // conservative test whether any voxel of the tile sees the element
+        __syncthreads();  // acc is zeroed; s_cnt of the previous pass is no longer read
+        // conservative tests in float32 whether any voxel of the tile sees the
+        // element and can reach this CTA's rows; then, for the tiles that
+        // pass, the float64 reference delay of element m to the tile centre
         const long long t = t0 + tid;
         bool cand = false;
         AdjTileRec rec;
@@ -77,14 +91,8 @@ __global__ void __launch_bounds__(ADJ_THREADS, 2) adjoint_kernel(const AdjArgs A
             double cx, cy, cz;
             tile_centre(g, tx, ty, tz, cx, cy, cz);
             const double Gx = cx - rx, Gy = cy - ry, Gz = cz - rz;
-            const double D0 = sqrt(Gx * Gx + Gy * Gy + Gz * Gz);
-            const double R0 = A.ad * D0;
-            const double Rf = floor(R0);
-            rec.gx = (float)Gx; rec.gy = (float)Gy; rec.gz = (float)Gz; rec.d0 = (float)D0;
-            rec.rf = (float)(R0 - Rf);
-            rec.rb = (int)Rf;
-            rec.tile = (int)t;
-            rec.pad = 0;
+            rec.gx = (float)Gx; rec.gy = (float)Gy; rec.gz = (float)Gz;
+            const float d0f = sqrtf(rec.gx * rec.gx + rec.gy * rec.gy + rec.gz * rec.gz);
             cand = true;
             if (A.thr >= 0.f) {
                 const float z0 = rec.gx * nn.x + rec.gy * nn.y + rec.gz * nn.z;
@@ -94,6 +102,24 @@ __global__ void __launch_bounds__(ADJ_THREADS, 2) adjoint_kernel(const AdjArgs A
                 const float zmax = z0 + A.tile_radius;
                 const float rmin = fmaxf(rho0 - A.tile_radius, 0.f);
                 cand = (zmax > 0.f) && (rmin * rmin <= A.thr * zmax * zmax * 1.001f);
+            }
+            if (cand) {
+                // rows k of the tile lie in tb + Rb + floor(rest + rf + offset) with
+                // |offset| <= a R: [span.x + Rb - aRi, span.y + Rb + aRi]; taps reach k + 1
+                const int rbf = (int)floorf(A.a * d0f);
+                const int2 sp = __ldg(A.tx_span + t);
+                const int klo = sp.x + rbf - A.aRi, khi = sp.y + rbf + A.aRi;
+                cand = klo < R1 && khi + 1 >= R0;
+            }
+            if (cand) {
+                const double D0 = sqrt(Gx * Gx + Gy * Gy + Gz * Gz);
+                const double Rd = A.ad * D0;
+                const double Rf = floor(Rd);
+                rec.d0 = (float)D0;
+                rec.rf = (float)(Rd - Rf);
+                rec.rb = (int)Rf;
+                rec.tile = (int)t;
+                rec.pad = 0;
             }
         }
         const unsigned bal = __ballot_sync(0xffffffffu, cand);
@@ -105,10 +131,12 @@ __global__ void __launch_bounds__(ADJ_THREADS, 2) adjoint_kernel(const AdjArgs A
             off += (w < warp) ? c : 0;
             total += c;
         }
-        if (cand) recs[off + __popc(bal & ((1u << lane) - 1u))] = rec;
+        if (cand) recs[nbuf + off + __popc(bal & ((1u << lane) - 1u))] = rec;
+        nbuf += total;
+        if (nbuf < ADJ_THREADS && t0 + ADJ_THREADS < ntiles) continue;  // gather more first
         __syncthreads();
 
-        for (int c = slot; c < total; c += ADJ_THREADS / 16) {
+        for (int c = slot; c < nbuf; c += ADJ_THREADS / 16) {
             const AdjTileRec R = recs[c];
             const int tile = R.tile;
             const int tx = tile % g.tiles_x;
@@ -164,7 +192,11 @@ __global__ void __launch_bounds__(ADJ_THREADS, 2) adjoint_kernel(const AdjArgs A
                 const int q = q0 + qq;
                 const size_t tq = (size_t)tile * A.Q + q;
                 const int kb = __ldg(A.tx_tb + tq) + R.rb;
-                float* const arow = acc + (size_t)qq * K * FB * C;
+                // this transmit's rows of the tile against the band
+                if (kb + (int)floorf(__ldg(A.tx_tmin + tq)) - A.aRi >= R1 ||
+                    kb + (int)floorf(__ldg(A.tx_tmax + tq)) + A.aRi + 2 < R0)
+                    continue;
+                float *const arow = acc + (size_t)qq * L * FB * C;  // row k at arow + (k - R0) FB C
                 // running rows kc and kc + 1 (kc = -4: none yet)
                 int kc = -4;
                 float a0[FB * C], a1[FB * C];
@@ -180,6 +212,7 @@ __global__ void __launch_bounds__(ADJ_THREADS, 2) adjoint_kernel(const AdjArgs A
                     const float al = f - fl;
                     const int k = kb + (int)fl;
                     if ((unsigned)k > (unsigned)(K - 2)) continue;
+                    if (k + 1 < R0 || k >= R1) continue;  // both taps outside the band
                     const float w = A.w_tx ? __ldg(A.w_tx + tq * TILE_N + vl) : 1.f;
                     float c0r, c0i = 0.f, c1r, c1i = 0.f;
                     if constexpr (IQ) {
@@ -194,16 +227,17 @@ __global__ void __launch_bounds__(ADJ_THREADS, 2) adjoint_kernel(const AdjArgs A
                         c0r = w * (1.f - al);
                         c1r = w * al;
                     }
-                    // rows kc, kc + 1 that the new pair (k, k + 1) no longer covers go to shared memory
+                    // rows kc, kc + 1 that the new pair (k, k + 1) no longer covers go to
+                    // shared memory (those of the band; the rest belong to other CTAs)
                     const bool keep0 = kc == k || kc == k + 1;
                     const bool keep1 = kc + 1 == k || kc + 1 == k + 1;
-                    if (kc >= 0 && !keep0) {
-                        float *p = arow + (size_t)kc * FB * C;
+                    if (kc >= R0 && kc < R1 && !keep0) {
+                        float *p = arow + (size_t)(kc - R0) * FB * C;
 #pragma unroll
                         for (int i = 0; i < FB * C; ++i) atomicAdd(p + i, a0[i]);
                     }
-                    if (kc >= 0 && !keep1) {
-                        float *p = arow + (size_t)(kc + 1) * FB * C;
+                    if (kc + 1 >= R0 && kc + 1 < R1 && !keep1) {
+                        float *p = arow + (size_t)(kc + 1 - R0) * FB * C;
 #pragma unroll
                         for (int i = 0; i < FB * C; ++i) atomicAdd(p + i, a1[i]);
                     }
@@ -242,16 +276,20 @@ __global__ void __launch_bounds__(ADJ_THREADS, 2) adjoint_kernel(const AdjArgs A
                         }
                     }
                 }
-                if (kc >= 0) {
-                    float *p = arow + (size_t)kc * FB * C;
+                if (kc >= R0 && kc < R1) {
+                    float *p = arow + (size_t)(kc - R0) * FB * C;
 #pragma unroll
-                    for (int i = 0; i < FB * C; ++i) {
-                        atomicAdd(p + i, a0[i]);
-                        atomicAdd(p + FB * C + i, a1[i]);
-                    }
+                    for (int i = 0; i < FB * C; ++i) atomicAdd(p + i, a0[i]);
+                }
+                if (kc + 1 >= R0 && kc + 1 < R1) {
+                    float *p = arow + (size_t)(kc + 1 - R0) * FB * C;
+#pragma unroll
+                    for (int i = 0; i < FB * C; ++i) atomicAdd(p + i, a1[i]);
                 }
             }
         }
+        __syncthreads();  // the buffered records are processed
+        nbuf = 0;
     }
     __syncthreads();
 
@@ -262,8 +300,8 @@ __global__ void __launch_bounds__(ADJ_THREADS, 2) adjoint_kernel(const AdjArgs A
         for (int b = 0; b < FB; ++b) {
             if (b0 + b >= A.B) break;
             const size_t row = (((size_t)(b0 + b) * A.Q + q) * A.M + m) * (size_t)K;
-            for (int k = tid; k < K; k += ADJ_THREADS) {
-                const float *a = acc + ((size_t)qq * K + k) * FB * C + b * C;
+            for (int k = R0 + tid; k < R1; k += ADJ_THREADS) {
+                const float *a = acc + ((size_t)qq * L + (k - R0)) * FB * C + b * C;
                 if constexpr (IQ) {
                     const float2 rt = A.rot ? A.rot[k] : make_float2(1.f, 0.f);
                     reinterpret_cast<float2 *>(A.y)[row + k] =
@@ -276,18 +314,20 @@ __global__ void __launch_bounds__(ADJ_THREADS, 2) adjoint_kernel(const AdjArgs A
     }
 }
 
-size_t adjoint_smem_bytes(int qc, int K, int fb, int iq) {
-    return sizeof(float) * (size_t)qc * K * fb * (iq ? 2 : 1) + sizeof(AdjTileRec) * ADJ_THREADS +
+size_t adjoint_smem_bytes(int qc, int rows, int fb, int iq) {
+    return sizeof(float) * (size_t)qc * rows * fb * (iq ? 2 : 1) + sizeof(AdjTileRec) * 2 * ADJ_THREADS +
            sizeof(int) * (ADJ_THREADS / 32);
 }
 
 template <bool IQ, int FB>
 static cudaError_t launch_adj_t(const AdjArgs &A, cudaStream_t s) {
-    const size_t smem = adjoint_smem_bytes(A.qc, A.K, FB, IQ);
+    const size_t smem = adjoint_smem_bytes(A.qc, A.rows, FB, IQ);
     auto kern = adjoint_kernel<IQ, FB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)A.M, (unsigned)((A.Q + A.qc - 1) / A.qc), (unsigned)((A.B + FB - 1) / FB));
+    const long long gy = (long long)((A.Q + A.qc - 1) / A.qc) * A.n_bands;
+    if (gy > 65535) return cudaErrorInvalidConfiguration;
+    dim3 grid((unsigned)A.M, (unsigned)gy, (unsigned)((A.B + FB - 1) / FB));
     kern<<<grid, ADJ_THREADS, smem, s>>>(A);
     return cudaGetLastError();
 }

@@ -68,6 +68,7 @@ struct das_plan {
     float *tx_t = nullptr;
     float *tx_tmin = nullptr;
     float *tx_tmax = nullptr;
+    int2 *tx_span = nullptr;
     int *err = nullptr;
     float *w_tx = nullptr;
     float2 *rot = nullptr;
@@ -95,7 +96,7 @@ struct das_plan {
     bool dirty = true;
     unsigned long long wait_ns = 0;  // test hook: limit of the kernels' pipeline waits (0: 1 s)
     int wait_probe = 0;              // test hook: one CTA waits on a barrier nothing arrives on
-    das_tuning_t tuning{0, 0, 0, 0, 0};
+    das_tuning_t tuning{};
     size_t bytes = 0;
     long long launches = 0;
     std::vector<cudaEvent_t> ev_start, ev_stop;
@@ -153,6 +154,7 @@ int sample_bytes_store(const das_plan *p) {
 }
 
 const int FB_F32[] = {20, 16, 12, 8, 4, 2, 1};
+constexpr int ADJ_ROWS = 256;  // sample rows per adjoint CTA (das_adjoint.cu); measured best of 32..K
 const int FB_16[] = {24, 20, 16, 12, 8, 4, 2, 1};
 
 // Frames per thread for a call with B frames: the supported value minimising
@@ -208,7 +210,7 @@ int ensure_scratch(das_plan *p) {
 int prepare_if_dirty(das_plan *p, cudaStream_t s) {
     if (!p->dirty) return DAS_OK;
     DAS_CU(launch_prepare(p->g, p->Q, p->tx_kind, p->tx_vec, p->tx_off, p->t0, p->fs / p->c, p->tx_tb, p->tx_t,
-                          p->tx_tmin, p->tx_tmax, s));
+                          p->tx_tmin, p->tx_tmax, p->tx_span, s));
     p->launches += 1;
     p->dirty = false;
     return DAS_OK;
@@ -556,6 +558,7 @@ int das_plan_create(das_plan_t **out, const das_geometry_t *geometry, const das_
     DAS_ALLOC(p->tx_t, sizeof(float) * (size_t)T * Q * TILE_N, "transmit delays");
     DAS_ALLOC(p->tx_tmin, sizeof(float) * (size_t)T * Q, "transmit delay minima");
     DAS_ALLOC(p->tx_tmax, sizeof(float) * (size_t)T * Q, "transmit delay maxima");
+    DAS_ALLOC(p->tx_span, sizeof(int2) * (size_t)T, "transmit row spans");
     DAS_ALLOC(p->err, sizeof(int), "device error word");
     if ((e0 = cudaMemset(p->err, 0, sizeof(int))) != cudaSuccess) return bail(cuda_fail(e0, "cudaMemset"));
     DAS_ALLOC(p->partial, sizeof(double) * (size_t)T * p->max_batch, "partials");
@@ -616,7 +619,7 @@ int das_plan_create(das_plan_t **out, const das_geometry_t *geometry, const das_
 
 void das_plan_destroy(das_plan_t *plan) {
     if (!plan) return;
-    DeviceGuard guard(plan->device);
+    DeviceGuard guard(plan->device);  // best effort: the plan is released in any case
     cudaDeviceSynchronize();
     destroy_events(plan);
     for (cudaStream_t cs : plan->copy_streams) cudaStreamDestroy(cs);
@@ -656,6 +659,7 @@ int das_plan_info(const das_plan_t *plan, das_plan_info_t *info) {
     info->tc_mma_items = 0;
     if (plan->tc_items) {
         DeviceGuard guard(plan->device);
+        if (!guard.ok) return fail(DAS_ERR_CUDA, "cannot select the plan's device");
         unsigned long long v = 0;
         DAS_CU(cudaMemcpy(&v, plan->tc_items, sizeof(v), cudaMemcpyDeviceToHost));
         info->tc_mma_items = (long long)v;
@@ -666,6 +670,7 @@ int das_plan_info(const das_plan_t *plan, das_plan_info_t *info) {
 int das_plan_check(das_plan_t *plan, das_stream_t stream) {
     if (!plan) return fail(DAS_ERR_INVALID_ARG, "plan is NULL");
     DeviceGuard guard(plan->device);
+    if (!guard.ok) return fail(DAS_ERR_CUDA, "cannot select the plan's device");
     int flags = 0;
     DAS_CU(cudaMemcpyAsync(&flags, plan->err, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
     DAS_CU(cudaStreamSynchronize((cudaStream_t)stream));
@@ -689,6 +694,7 @@ int das_plan_set_wait_test(das_plan_t *plan, long long wait_ns, int probe) {
 int das_plan_enable_timing(das_plan_t *plan, int capacity) {
     if (!plan || capacity < 0) return fail(DAS_ERR_INVALID_ARG, "bad argument");
     DeviceGuard guard(plan->device);
+    if (!guard.ok) return fail(DAS_ERR_CUDA, "cannot select the plan's device");
     destroy_events(plan);
     for (int i = 0; i < capacity; ++i) {
         cudaEvent_t a, b;
@@ -706,6 +712,7 @@ int das_plan_enable_timing(das_plan_t *plan, int capacity) {
 int das_plan_timing(das_plan_t *plan, double *ms_total, int *launches) {
     if (!plan || !ms_total || !launches) return fail(DAS_ERR_INVALID_ARG, "NULL argument");
     DeviceGuard guard(plan->device);
+    if (!guard.ok) return fail(DAS_ERR_CUDA, "cannot select the plan's device");
     double total = 0.0;
     for (int i = 0; i < plan->ev_used; ++i) {
         DAS_CU(cudaEventSynchronize(plan->ev_stop[i]));
@@ -724,6 +731,9 @@ int das_plan_set_tuning(das_plan_t *plan, const das_tuning_t *tuning) {
     if (tuning->frames_per_thread < 0 || tuning->ctas_per_sm < 0 || tuning->staging < 0 || tuning->tensor_cores < 0 ||
         tuning->tc_chain < -1)
         return fail(DAS_ERR_INVALID_ARG, "negative tuning value");
+    if (tuning->voxels_per_thread < 0 || tuning->voxels_per_thread > 2)
+        return fail(DAS_ERR_INVALID_ARG, "voxels_per_thread must be 0, 1 or 2");
+    if (tuning->adjoint_rows < 0) return fail(DAS_ERR_INVALID_ARG, "adjoint_rows must be >= 0");
     if (tuning->tensor_cores && !tc_capable(plan))
         return fail(DAS_ERR_UNSUPPORTED, "the tensor-core path takes IQ data stored as f16 or bf16");
     if (tuning->load_width != 0 && tuning->load_width != 128 && tuning->load_width != 256)
@@ -732,6 +742,7 @@ int das_plan_set_tuning(das_plan_t *plan, const das_tuning_t *tuning) {
         !tile_fb_supported(MODE_FWD, is_iq(plan), plan->storage, tuning->frames_per_thread))
         return fail(DAS_ERR_UNSUPPORTED, "frames_per_thread %d not compiled for this storage", tuning->frames_per_thread);
     DeviceGuard guard(plan->device);
+    if (!guard.ok) return fail(DAS_ERR_CUDA, "cannot select the plan's device");
     plan->tuning = *tuning;
     int rc = ensure_scratch(plan);
     if (rc == DAS_OK && tuning->tensor_cores) rc = ensure_tc_scratch(plan);
@@ -767,7 +778,10 @@ int das_forward(das_plan_t *plan, const void *y_dev, void *x_dev, int batch, das
     A.x = x_dev;
     const bool timed = plan->ev_used < (int)plan->ev_start.size();
     if (timed) DAS_CU(cudaEventRecord(plan->ev_start[plan->ev_used], s));
-    DAS_CU(launch_tile(A, MODE_FWD, is_iq(plan), plan->storage, fb, nch, s));
+    if (col && plan->tuning.voxels_per_thread == 2 && pair_supported(MODE_FWD, is_iq(plan), plan->storage, fb))
+        DAS_CU(launch_pair(A, plan->storage, fb, nch, s));
+    else
+        DAS_CU(launch_tile(A, MODE_FWD, is_iq(plan), plan->storage, fb, nch, s));
     plan->launches += 1;
     if (timed) {
         DAS_CU(cudaEventRecord(plan->ev_stop[plan->ev_used], s));
@@ -820,6 +834,7 @@ int das_forward_host(das_plan_t *plan, const void *y_host, void *x_host, int bat
     int rc = check_call(plan, y_host, x_host, batch);
     if (rc != DAS_OK) return rc;
     DeviceGuard guard(plan->device);
+    if (!guard.ok) return fail(DAS_ERR_CUDA, "cannot select the plan's device");
     cudaStream_t s = (cudaStream_t)stream;
     if ((rc = ensure_host_io(plan, 1)) != DAS_OK) return rc;
     const size_t yb = (size_t)batch * plan->Q * plan->M * plan->K * sample_bytes_public(plan);
@@ -909,6 +924,7 @@ int das_forward_host_many(das_plan_t *plan, const void *const *y_host, void *con
     for (int i = 0; i < n_batches; ++i)
         if ((rc = check_call(plan, y_host[i], x_host[i], batch)) != DAS_OK) return rc;
     DeviceGuard guard(plan->device);
+    if (!guard.ok) return fail(DAS_ERR_CUDA, "cannot select the plan's device");
     cudaStream_t s = (cudaStream_t)stream;
     if ((rc = ensure_host_io(plan, 2)) != DAS_OK) return rc;
     rc = forward_host_many_run(plan, y_host, x_host, n_batches, batch, s);
@@ -986,23 +1002,31 @@ int das_adjoint(das_plan_t *plan, const void *x_dev, void *y_dev, int batch, das
     int rc = check_call(plan, x_dev, y_dev, batch);
     if (rc != DAS_OK) return rc;
     DeviceGuard guard(plan->device);
+    if (!guard.ok) return fail(DAS_ERR_CUDA, "cannot select the plan's device");
     cudaStream_t s = (cudaStream_t)stream;
     if ((rc = prepare_if_dirty(plan, s)) != DAS_OK) return rc;
     const bool iq = is_iq(plan);
     const size_t esz = iq ? 8 : 4;
-    const size_t budget = 96 * 1024;  // two CTAs of 512 threads per SM
+    // each CTA owns a band of ADJ_ROWS samples of its element's rows (all
+    // transmits of a chunk, fb frames) in shared memory
+    const int want = plan->tuning.adjoint_rows > 0 ? plan->tuning.adjoint_rows : ADJ_ROWS;
+    const int rows = plan->K < want ? plan->K : want;
+    const size_t budget = 64 * 1024;  // two CTAs of 512 threads per SM
     int fb = 1, qc = 0;
     const int fbs[3] = {4, 2, 1};
     for (int i = 0; i < 3; ++i) {
         const int f = fbs[i];
         if (f > 1 && f > batch) continue;
-        const size_t row = (size_t)plan->K * f * esz;
+        const size_t row = (size_t)rows * f * esz;
         const int qmax = (int)(budget / row);
         if (qmax >= (plan->Q < 4 ? plan->Q : 4) || (f == 1 && qmax >= 1)) { fb = f; qc = qmax; break; }
     }
-    if (qc < 1) return fail(DAS_ERR_UNSUPPORTED, "n_samples %d too large for the adjoint's shared-memory rows", plan->K);
+    if (qc < 1) return fail(DAS_ERR_UNSUPPORTED, "the adjoint's shared-memory rows do not fit");
+    if (qc > plan->Q) qc = plan->Q;
     const int nqc = (plan->Q + qc - 1) / qc;
     qc = (plan->Q + nqc - 1) / nqc;
+    const int n_bands = (plan->K + rows - 1) / rows;
+    if ((long long)nqc * n_bands > 65535) return fail(DAS_ERR_UNSUPPORTED, "n_samples %d too large for the adjoint grid", plan->K);
     AdjArgs A{};
     A.g = plan->g;
     A.M = plan->M;
@@ -1016,6 +1040,12 @@ int das_adjoint(das_plan_t *plan, const void *x_dev, void *y_dev, int batch, das
     A.elem_nrm = plan->elem_nrm;
     A.tx_tb = plan->tx_tb;
     A.tx_t = plan->tx_t;
+    A.tx_tmin = plan->tx_tmin;
+    A.tx_tmax = plan->tx_tmax;
+    A.tx_span = plan->tx_span;
+    A.rows = rows;
+    A.n_bands = n_bands;
+    A.aRi = (int)ceil((double)A.a * (double)A.tile_radius) + 2;
     A.w_tx = plan->w_tx;
     A.rot = plan->rot;
     A.x = x_dev;
@@ -1033,6 +1063,7 @@ int das_grad_c(das_plan_t *plan, const void *y_dev, const void *gx_dev, double *
     if (!dLdc_dev || !aligned(dLdc_dev, 8)) return fail(DAS_ERR_INVALID_ARG, "dLdc_dev must be an aligned device double");
     if (plan->storage != DAS_STORE_F32) return fail(DAS_ERR_UNSUPPORTED, "das_grad_c needs float32 storage");
     DeviceGuard guard(plan->device);
+    if (!guard.ok) return fail(DAS_ERR_CUDA, "cannot select the plan's device");
     cudaStream_t s = (cudaStream_t)stream;
     if ((rc = prepare_if_dirty(plan, s)) != DAS_OK) return rc;
     const int fb = choose_fb(plan, batch, MODE_DC);
@@ -1056,6 +1087,7 @@ int das_count_active(das_plan_t *plan, long long *count_host, das_stream_t strea
     g_err[0] = 0;
     if (!plan || !count_host) return fail(DAS_ERR_INVALID_ARG, "NULL argument");
     DeviceGuard guard(plan->device);
+    if (!guard.ok) return fail(DAS_ERR_CUDA, "cannot select the plan's device");
     cudaStream_t s = (cudaStream_t)stream;
     int rc;
     if ((rc = prepare_if_dirty(plan, s)) != DAS_OK) return rc;
@@ -1160,7 +1192,7 @@ struct das_batch {
     das_plan *plans[BATCH_MAX_PLANS] = {nullptr};
     int frames[BATCH_MAX_PLANS] = {0};
     int fb = 0;
-    das_tuning_t tuning{0, 0, 0, 0};
+    das_tuning_t tuning{};
     int4 *items = nullptr;
     int n_items = 0;
     int *counter = nullptr;
@@ -1270,6 +1302,10 @@ extern "C" int das_batch_create(das_batch_t **out, das_plan_t *const *plans, con
     b->device = plans[0]->device;
     for (int i = 0; i < n_plans; ++i) { b->plans[i] = plans[i]; b->frames[i] = frames[i]; }
     DeviceGuard guard(b->device);
+    if (!guard.ok) {
+        delete b;
+        return fail(DAS_ERR_CUDA, "cannot select the plans' device");
+    }
     int rc = DAS_OK;
     cudaError_t e;
     if ((e = cudaMalloc(&b->counter, sizeof(int))) != cudaSuccess) rc = cuda_fail(e, "cudaMalloc(counter)");
@@ -1288,7 +1324,7 @@ extern "C" int das_batch_create(das_batch_t **out, das_plan_t *const *plans, con
 
 extern "C" void das_batch_destroy(das_batch_t *b) {
     if (!b) return;
-    DeviceGuard guard(b->device);
+    DeviceGuard guard(b->device);  // best effort: the batch is released in any case
     cudaDeviceSynchronize();
     batch_drop_graph(b);
     if (b->items) cudaFree(b->items);
@@ -1303,6 +1339,7 @@ extern "C" int das_batch_set_tuning(das_batch_t *b, const das_tuning_t *tuning) 
         return fail(DAS_ERR_INVALID_ARG, "negative tuning value");
     if (tuning->tensor_cores) return fail(DAS_ERR_UNSUPPORTED, "the batched launch runs on the CUDA cores");
     DeviceGuard guard(b->device);
+    if (!guard.ok) return fail(DAS_ERR_CUDA, "cannot select the plan's device");
     b->tuning = *tuning;
     return batch_build(b);
 }
@@ -1324,6 +1361,7 @@ extern "C" int das_batch_forward(das_batch_t *b, const void *const *y_dev, void 
             return fail(DAS_ERR_INVALID_ARG, "plan %d: NULL or misaligned data pointer", i);
     }
     DeviceGuard guard(b->device);
+    if (!guard.ok) return fail(DAS_ERR_CUDA, "cannot select the plan's device");
     cudaStream_t s = (cudaStream_t)stream;
     int rc;
     for (int i = 0; i < b->n; ++i)

@@ -1,15 +1,17 @@
 // das_async.cuh -- mbarrier and bulk asynchronous copy helpers (inline PTX,
 // sm_103a) shared by the staged tile kernel and the tensor-core kernel.
 //
-// Every wait is bounded: a caller that sees a wait expire records the failure
-// in the plan's error word and leaves instead of spinning forever.
+// Every wait is bounded by wall time (%globaltimer): a caller that sees a wait
+// expire records the failure in the plan's error word and leaves instead of
+// spinning forever.  An iteration count is no bound: one try_wait may suspend
+// the thread for a system-dependent time.
 #pragma once
 
 #include <stdint.h>
 
 namespace das {
 
-constexpr uint32_t TMA_WAIT_LIMIT = 1u << 22;
+constexpr uint64_t WAIT_NS = 1000000000ull;  // 1 s
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -45,20 +47,6 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return done != 0;
 }
 
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-    for (uint32_t i = 0; i < TMA_WAIT_LIMIT; ++i)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
-
-// The same, also giving up once *flag is set (another warp of the CTA gave up).
-__device__ __forceinline__ bool mbar_wait_bounded_or(uint64_t *bar, uint32_t parity, const volatile int *flag) {
-    for (uint32_t i = 0; i < TMA_WAIT_LIMIT; ++i) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((i & 63u) == 63u && *flag) return false;
-    }
-    return false;
-}
 
 __device__ __forceinline__ uint64_t global_ns() {
     uint64_t t;
@@ -66,11 +54,16 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
-// Wait bounded by wall time (ns); false when the limit ran out.
-__device__ __forceinline__ bool mbar_wait_ns(uint64_t *bar, uint32_t parity, uint64_t ns) {
+// Wait bounded by wall time (ns); false when the limit ran out, or as soon as
+// *flag is set when a flag is given (another warp of the CTA gave up).
+__device__ __forceinline__ bool mbar_wait_ns(uint64_t *bar, uint32_t parity, uint64_t ns,
+                                             const volatile int *flag = nullptr) {
+    if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
-    while (!mbar_try_wait(bar, parity))
+    while (!mbar_try_wait(bar, parity)) {
+        if (flag && *flag) return false;
         if (global_ns() - t0 > ns) return false;
+    }
     return true;
 }
 

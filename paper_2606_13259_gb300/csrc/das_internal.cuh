@@ -122,6 +122,12 @@ struct AdjArgs {
     const float4 *elem_nrm;
     const int *tx_tb;
     const float *tx_t;
+    const float *tx_tmin;  // [tiles][Q] smallest / largest transmit rest over a tile's voxels
+    const float *tx_tmax;
+    const int2 *tx_span;   // [tiles] transmit row span over all transmits
+    int rows;              // sample rows per band: CTA band r owns rows [r * rows, (r + 1) * rows)
+    int n_bands;           // bands per (element, transmit chunk)
+    int aRi;               // ceil(a x tile radius) + 2: receive offset bound in rows, with margin
     const float *w_tx;
     const float2 *rot;   // [K] e^{i theta k} (IQ), or null
     const void *x;       // image [B][N]
@@ -131,9 +137,13 @@ struct AdjArgs {
 // Kernel launchers (defined in the .cu files).
 cudaError_t launch_prepare(const GridDesc &g, int Q, const int *kind, const double *vec, const double *off,
                            const double *t0, double ad, int *tx_tb, float *tx_t, float *tx_tmin, float *tx_tmax,
-                           cudaStream_t s);
+                           int2 *tx_span, cudaStream_t s);
 cudaError_t launch_tile(const TileArgs &args, int mode, int iq, int store, int fb, int n_chunks, cudaStream_t s);
 cudaError_t launch_adjoint(const AdjArgs &args, int iq, cudaStream_t s);
+// Forward kernel with two x-adjacent voxels per thread sharing sample rows
+// (das_tile_pair.cuh): float32 IQ rows in column order.
+bool pair_supported(int mode, int iq, int store, int fb);
+cudaError_t launch_pair(const TileArgs &A, int store, int fb, int n_chunks, cudaStream_t s);
 cudaError_t launch_reduce(const double *partial, long long n, double *out, cudaStream_t s);
 bool tile_fb_supported(int mode, int iq, int store, int fb);
 // Whether rows of fb samples can be read in column order (whole 16-byte

@@ -28,14 +28,16 @@ __device__ inline double tx_path(int kind, double vx, double vy, double vz, doub
 }
 
 // One CTA per tile, one thread per voxel lane.  Also records, per (tile,
-// transmit), the smallest float32 rest over the tile's voxels: together with
-// the tile radius it bounds the sample rows any voxel of the tile can need.
+// transmit), the smallest and largest float32 rest over the tile's voxels:
+// together with the tile radius they bound the sample rows any voxel of the
+// tile can need; and per tile the row span of the transmit part over all
+// transmits, tb + floor(rest) from its smallest to its largest value + 1.
 __global__ void __launch_bounds__(TILE_N) prepare_kernel(GridDesc g, int Q, const int *__restrict__ kind,
                                                          const double *__restrict__ vec,
                                                          const double *__restrict__ off, double t0x, double t0y,
                                                          double t0z, double ad, int *__restrict__ tx_tb,
                                                          float *__restrict__ tx_t, float *__restrict__ tx_tmin,
-                                                         float *__restrict__ tx_tmax) {
+                                                         float *__restrict__ tx_tmax, int2 *__restrict__ tx_span) {
     __shared__ float red[TILE_N / 32], red_max[TILE_N / 32];
     const long long tile = blockIdx.x;
     const int tx = (int)(tile % g.tiles_x);
@@ -49,6 +51,7 @@ __global__ void __launch_bounds__(TILE_N) prepare_kernel(GridDesc g, int Q, cons
     const double px = g.ox + g.sx * (tx * TILE_X + lx);
     const double py = g.oy + g.sy * (ty * TILE_Y + ly);
     const double pz = g.oz + g.sz * (tz * TILE_Z + lz);
+    int span_lo = 0x7fffffff, span_hi = -0x7fffffff;  // thread 0: transmit row span over all q
     for (int q = 0; q < Q; ++q) {
         const int kd = kind[q];
         const double vx = vec[3 * q], vy = vec[3 * q + 1], vz = vec[3 * q + 2], o = off[q];
@@ -74,17 +77,22 @@ __global__ void __launch_bounds__(TILE_N) prepare_kernel(GridDesc g, int Q, cons
             }
             tx_tmin[tile * Q + q] = m;
             if (tx_tmax) tx_tmax[tile * Q + q] = u;
+            if (m <= u) {  // the tile has voxels inside the grid
+                span_lo = min(span_lo, (int)base + (int)floorf(m));
+                span_hi = max(span_hi, (int)base + (int)floorf(u) + 1);
+            }
         }
         __syncthreads();
     }
+    if (threadIdx.x == 0 && tx_span) tx_span[tile] = make_int2(span_lo, span_hi);
 }
 
 cudaError_t launch_prepare(const GridDesc &g, int Q, const int *kind, const double *vec, const double *off,
                            const double *t0, double ad, int *tx_tb, float *tx_t, float *tx_tmin, float *tx_tmax,
-                           cudaStream_t s) {
+                           int2 *tx_span, cudaStream_t s) {
     const long long nt = n_tiles(g);
     prepare_kernel<<<(unsigned)nt, TILE_N, 0, s>>>(g, Q, kind, vec, off, t0[0], t0[1], t0[2], ad, tx_tb, tx_t,
-                                                   tx_tmin, tx_tmax);
+                                                   tx_tmin, tx_tmax, tx_span);
     return cudaGetLastError();
 }
 

@@ -250,6 +250,38 @@ template <int FB, bool IQ, int ST> struct FrameAcc {
         }
     }
 
+    // acc += c0 * tap0 + c1 * tap1 + c2 * tap2 (three rows; even FB, IQ):
+    // the second voxel of a thread pair, whose two taps sit at two of three
+    // rows loaded once for both voxels (das_tile_pair.cuh)
+    template <int G>
+    __device__ __forceinline__ void add3(int g0, const uint32_t *w0, const uint32_t *w1, const uint32_t *w2,
+                                         float c0r, float c0i, float c1r, float c1i, float c2r, float c2i) {
+        static_assert(PAIR && IQ, "three-row updates are for pair-planar IQ rows");
+        const float2 C0R = make_float2(c0r, c0r), C0I = make_float2(c0i, c0i), N0I = make_float2(-c0i, -c0i);
+        const float2 C1R = make_float2(c1r, c1r), C1I = make_float2(c1i, c1i), N1I = make_float2(-c1i, -c1i);
+        const float2 C2R = make_float2(c2r, c2r), C2I = make_float2(c2i, c2i), N2I = make_float2(-c2i, -c2i);
+#pragma unroll
+        for (int p = 0; p < G / 2; ++p) {
+            float2 zr0, zi0, zr1, zi1, zr2, zi2;
+            pair(w0, p, zr0, zi0);
+            pair(w1, p, zr1, zi1);
+            pair(w2, p, zr2, zi2);
+            const int q = g0 / 2 + p;
+            re2[q] = __ffma2_rn(C0R, zr0, re2[q]);
+            re2[q] = __ffma2_rn(N0I, zi0, re2[q]);
+            re2[q] = __ffma2_rn(C1R, zr1, re2[q]);
+            re2[q] = __ffma2_rn(N1I, zi1, re2[q]);
+            re2[q] = __ffma2_rn(C2R, zr2, re2[q]);
+            re2[q] = __ffma2_rn(N2I, zi2, re2[q]);
+            im2[q] = __ffma2_rn(C0R, zi0, im2[q]);
+            im2[q] = __ffma2_rn(C0I, zr0, im2[q]);
+            im2[q] = __ffma2_rn(C1R, zi1, im2[q]);
+            im2[q] = __ffma2_rn(C1I, zr1, im2[q]);
+            im2[q] = __ffma2_rn(C2R, zi2, im2[q]);
+            im2[q] = __ffma2_rn(C2I, zr2, im2[q]);
+        }
+    }
+
     __device__ __forceinline__ float re(int b) const {
         if constexpr (PAIR) return (b & 1) ? re2[b >> 1].y : re2[b >> 1].x;
         else return re1[b];

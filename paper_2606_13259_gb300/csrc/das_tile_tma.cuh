@@ -21,9 +21,10 @@
 // span of floor(f) + 1 over the tile is at most 4 a R + 3 rows.  A voxel whose
 // rows fall outside the window anyway reads them from global memory.
 //
-// Waits on the mbarriers are bounded; on expiry the kernel sets bit 0 of the
-// plan's error word, waits (bounded) for the copies it has in flight and
-// returns.
+// Waits on the mbarriers are bounded by 1 s of wall time; on expiry the warp
+// sets bit 0 of the plan's error word and a flag in shared memory on which the
+// other warps' waits give up too, then the CTA waits (bounded) for the copies
+// it has in flight and returns.
 #pragma once
 
 #include "das_async.cuh"
@@ -123,7 +124,7 @@ __device__ __forceinline__ bool tile_tma_body(const TileArgs &A, const long long
         const int j = i / Q, q = i - j * Q;
         const long long gi = g0 + i;
         if (gi >= TMA_STAGES &&
-            !mbar_wait_bounded_or(&ebar[gi % TMA_STAGES], (uint32_t)(((gi / TMA_STAGES) - 1) & 1), s_abort))
+            !mbar_wait_ns(&ebar[gi % TMA_STAGES], (uint32_t)(((gi / TMA_STAGES) - 1) & 1), WAIT_NS, s_abort))
             return false;
         uint64_t *bar = &mbar[gi % TMA_STAGES];
         int ks, cnt;
@@ -220,12 +221,18 @@ __device__ __forceinline__ bool tile_tma_body(const TileArgs &A, const long long
             }
             const long long gi = g0 + i;
             const int st = (int)(gi % TMA_STAGES);
-            if (*abort_flag) break;  // warp-uniform: one shared word, read by the whole warp
+            // warp-uniform decision: thread 0 may set the flag in its refill wait
+            // while the other lanes of its warp are already past this point, so
+            // the warp reconverges here and leaves together (a lane that left
+            // alone would leave the others waiting at __syncwarp below)
+            if (__any_sync(0xffffffffu, *abort_flag != 0)) break;
             // test hook (das_plan_set_wait_test): warp 1 of the first CTA waits
             // on a barrier nothing arrives on for its first item, so it runs out
             const bool probe = A.probe && tile == 0 && chunk == 0 && gi == 0 && warp == 1;
-            const bool timed_out = probe ? !mbar_wait_ns(pbar, 0u, A.wait_ns ? A.wait_ns : 1000000000ull)
-                                         : !mbar_wait_bounded(&mbar[st], (uint32_t)((gi / TMA_STAGES) & 1));
+            // (a warp that gives up because another one did takes the same exit)
+            const bool timed_out = probe ? !mbar_wait_ns(pbar, 0u, A.wait_ns ? A.wait_ns : WAIT_NS)
+                                         : !mbar_wait_ns(&mbar[st], (uint32_t)((gi / TMA_STAGES) & 1), WAIT_NS,
+                                                         abort_flag);
             if (__any_sync(0xffffffffu, timed_out)) {
                 if (lane == 0) atomicOr(A.err, 1);
                 *abort_flag = 1;
@@ -310,7 +317,7 @@ __device__ __forceinline__ bool tile_tma_body(const TileArgs &A, const long long
                 // earlier one was waited for through its stage's empty barrier)
                 for (int d = n_issued - 1; d >= 0 && d >= n_issued - TMA_STAGES; --d) {
                     const long long gd = g0 + d;
-                    mbar_wait_bounded(&mbar[gd % TMA_STAGES], (uint32_t)((gd / TMA_STAGES) & 1));
+                    mbar_wait_ns(&mbar[gd % TMA_STAGES], (uint32_t)((gd / TMA_STAGES) & 1), WAIT_NS);
                 }
             }
         }

@@ -41,6 +41,22 @@ def test_adjoint_matches_oracle(das, oracle, case, B):
     plan.close()
 
 
+@pytest.mark.parametrize("rows", [7, 16, 64, 0, 100000])
+@pytest.mark.parametrize("case", [0, 3])
+def test_adjoint_row_bands(das, oracle, case, rows):
+    """Bands of 7, 16, 64 (and the automatic height) sample rows per CTA, and
+    one band holding all K rows: every band boundary splits the interpolation
+    taps of some terms between two CTAs, which must still add up exactly."""
+    sc = ragged_scene(*RAGGED[case])
+    B = 2
+    x = image_like(sc, B, seed=80 + case)
+    plan = das.Plan.from_scene(sc, max_batch=B)
+    plan.set_tuning(adjoint_rows=rows)
+    y = plan.adjoint(x.cuda().reshape((B,) + plan.shape)).cpu().numpy()
+    plan.close()
+    assert_parity(y, oracle.adjoint(sc, x.numpy()).reshape(y.shape), TOL_F32, what=f"adjoint, {rows} rows per band")
+
+
 @pytest.mark.parametrize("B", [9, 45])
 def test_adjoint_and_grad_c_large_batches(das, oracle, B):
     """Batches that span several frame chunks of the adjoint and of the

@@ -220,6 +220,37 @@ def test_staged_and_global_sample_windows(das, oracle, staging, load_width, fb, 
     print(f"fb {fb} {storage} staging={staging} width={load_width}: relative L2 {e2:.3e}, element-wise {em:.3e}")
 
 
+PAIR_SCENES = {
+    # odd number of tiles along x (the last block holds one tile), three transmit kinds
+    "ragged_odd_tiles": lambda: ragged_scene(*RAGGED[3]),
+    # x spacing 0.3 mm: neighbours along x up to ~3 samples apart, so the
+    # separate-rows branch of the pair kernel runs beside the shared-row one
+    "wide_x_spacing": lambda: S.scene_tiny(iq=True, n=(21, 6, 9), elems=(5, 4), n_tx=3, f_number=0.8,
+                                           K=160).with_(spacing=(0.3e-3, 0.1e-3, 0.1e-3)),
+    # paper geometry, a crop with ragged tiles
+    "paper_crop": lambda: S.scene_paper(512).with_(nx=40, ny=10, nz=9),
+}
+
+
+@pytest.mark.parametrize("name", sorted(PAIR_SCENES))
+@pytest.mark.parametrize("B,fb", [(3, 4), (8, 8), (20, 20), (23, 12)])
+def test_pair_kernel_matches_oracle_and_single_voxel_kernel(das, oracle, name, B, fb):
+    """Two x-adjacent voxels per thread sharing rows (the float32 IQ default)
+    against the oracle and against the one-voxel-per-thread kernel."""
+    sc = PAIR_SCENES[name]()
+    y = S.random_channels(sc, B, seed=90 + fb)
+    ref = oracle.forward(sc, y.numpy())
+    out = {}
+    for vpt in (1, 2):
+        plan = das.Plan.from_scene(sc, max_batch=B)
+        plan.set_tuning(frames_per_thread=fb, voxels_per_thread=vpt)
+        out[vpt] = plan.forward(y.cuda()).cpu().numpy().reshape(B, -1)
+        plan.check()
+        plan.close()
+        assert_parity(out[vpt], ref, TOL_F32, what=f"{name}, {vpt} voxels per thread, fb {fb}")
+    assert_parity(out[2], out[1], TOL_F32, what=f"{name}: pair kernel against the one-voxel kernel")
+
+
 def test_staged_paper_tile_geometry_small_batch(das, oracle):
     """Paper geometry cropped to 32 x 24 x 20 voxels (ragged tiles), 4 frames:
     staged windows against the oracle on every voxel."""
