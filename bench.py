@@ -376,7 +376,8 @@ def run_batched(args):
         "vs_baseline": None, "dtype": "f16 storage, f32 arithmetic", "data": "synthetic",
         "config": {"workload": "batched_3plans_64frames",
                    "plans": [dict(sc.describe(), frames=f) for sc, f in zip(scenes, frames)],
-                   "tuning": {k: tuned[k] for k in ("frames_per_thread", "ctas_per_sm", "staging")},
+                   "tuning": {k: tuned.get(k) for k in ("frames_per_thread", "ctas_per_sm", "staging",
+                                                         "plan_tensor_cores")},
                    "work_items": info["work_items"]},
         "per_plan_volumes_per_s_in_batch": [f / (ms * 1e-3) for f in frames],
         "per_plan_volumes_per_s_alone": alone,

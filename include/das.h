@@ -270,8 +270,12 @@ int das_count_active(das_plan_t *plan, long long *count_host, das_stream_t strea
  * and transmit counts, one sample type and storage -- and all their frames in
  * one persistent kernel launch.  The CTAs of the persistent grid take
  * (plan, frame chunk, voxel tile) items from an atomic work counter, heaviest
- * plans first, and run the forward tile body with that plan's arguments.  The
- * per-plan relayouts, the counter reset and the persistent launch are captured
+ * plans first, and run the forward tile body with that plan's arguments.  A
+ * plan whose own tuning selects the tensor cores (das_plan_set_tuning,
+ * tensor_cores = 1, f16 / bf16 IQ) is taken out of the work list and runs as
+ * its own tensor-core launches (Sec. 3.4) in the same graph; that choice is
+ * read when the batch is built (das_batch_create, das_batch_set_tuning).  The
+ * per-plan relayouts, the counter reset and the launches are captured
  * once into a CUDA graph and replayed; a call with other data pointers
  * captures a new graph.  Up to 8 plans; frames[i] <= max_batch of plan i.
  * das_batch_create allocates the work list and may enlarge a plan's scratch;

@@ -63,17 +63,28 @@ def _time(fn, reps: int, warmup: int) -> float:
     return e0.elapsed_time(e1) / reps
 
 
+def _set_plan_tc(batch: Batch, flags) -> None:
+    for p, on in zip(batch.plans, flags):
+        p.set_tuning(tensor_cores=bool(on))
+
+
 def tune_batch(batch: Batch, ys, outs, fbs: Optional[Iterable[int]] = None,
                ctas: Iterable[int] = (0, 1, 2, 3), staging=(False, True), reps: int = 3, warmup: int = 1,
-               use_cache: bool = True) -> dict:
-    """Pick (frames per thread, CTAs per SM, staged windows) for a batch; applies and returns it."""
+               use_cache: bool = True, tensor_cores: bool = True) -> dict:
+    """Pick (frames per thread, CTAs per SM, staged windows) for a batch, and
+    for each plan that can take them whether it runs on the tensor cores
+    (greedily, heaviest plan first, each kept only if the whole batch gets
+    faster); applies and returns it."""
     key = "batch:" + torch.cuda.get_device_name() + ":" + ";".join(
         f"{_plan_sig(p)}/B{f}" for p, f in zip(batch.plans, batch.frames))
     if use_cache:
         hit = _load().get(key)
         if hit:
+            _set_plan_tc(batch, hit.get("plan_tensor_cores", [False] * len(batch.plans)))
             batch.set_tuning(hit["frames_per_thread"], hit["ctas_per_sm"], hit.get("staging", False))
             return dict(hit, cached=True)
+    tc_flags = [False] * len(batch.plans)
+    _set_plan_tc(batch, tc_flags)
     p0 = batch.plans[0]
     if fbs is None:
         fbs = F32_FB if p0.storage == "f32" else F16_FB
@@ -89,8 +100,26 @@ def tune_batch(batch: Batch, ys, outs, fbs: Optional[Iterable[int]] = None,
                 results.append({"frames_per_thread": fb, "ctas_per_sm": c, "staging": st, "ms": ms})
     best = min(results, key=lambda r: r["ms"])
     batch.set_tuning(best["frames_per_thread"], best["ctas_per_sm"], best["staging"])
+    best_ms = best["ms"]
+    if tensor_cores:
+        order = sorted(range(len(batch.plans)), key=lambda i: -batch.plans[i].M * batch.plans[i].Q * batch.frames[i])
+        for i in order:
+            p = batch.plans[i]
+            if not (p.iq and p.storage in ("f16", "bf16")):
+                continue
+            trial = list(tc_flags)
+            trial[i] = True
+            _set_plan_tc(batch, trial)
+            batch.set_tuning(best["frames_per_thread"], best["ctas_per_sm"], best["staging"])
+            ms = _time(lambda: batch.forward(ys, outs), reps, warmup)
+            results.append({"frames_per_thread": best["frames_per_thread"], "ctas_per_sm": best["ctas_per_sm"],
+                            "staging": best["staging"], "plan_tensor_cores": trial, "ms": ms})
+            if ms < best_ms:
+                tc_flags, best_ms = trial, ms
+        _set_plan_tc(batch, tc_flags)
+        batch.set_tuning(best["frames_per_thread"], best["ctas_per_sm"], best["staging"])
     out = {"frames_per_thread": best["frames_per_thread"], "ctas_per_sm": best["ctas_per_sm"],
-           "staging": best["staging"], "ms": best["ms"], "candidates": results}
+           "staging": best["staging"], "plan_tensor_cores": tc_flags, "ms": best_ms, "candidates": results}
     if use_cache:
         _store(key, out)
     return dict(out, cached=False)

@@ -1191,6 +1191,7 @@ struct das_batch {
     int n = 0;
     das_plan *plans[BATCH_MAX_PLANS] = {nullptr};
     int frames[BATCH_MAX_PLANS] = {0};
+    bool tc[BATCH_MAX_PLANS] = {false};  // plan runs as its own tensor-core launches inside the graph
     int fb = 0;
     das_tuning_t tuning{};
     int4 *items = nullptr;
@@ -1223,7 +1224,8 @@ int batch_choose_fb(const das_batch *b) {
     for (int fb : cands) {
         if (!batch_fb_supported(is_iq(p), p->storage, fb)) continue;
         long cost = 0;
-        for (int i = 0; i < b->n; ++i) cost += (long)((b->frames[i] + fb - 1) / fb) * (6 + fb);
+        for (int i = 0; i < b->n; ++i)
+            if (!b->tc[i]) cost += (long)((b->frames[i] + fb - 1) / fb) * (6 + fb);
         if (best_cost < 0 || cost < best_cost) { best_cost = cost; best = fb; }
     }
     return best;
@@ -1242,8 +1244,11 @@ int ensure_scratch_frames(das_plan *p, int bs) {
     return rc;
 }
 
-// Work list: (plan, chunk, tile), the plans with the most work per tile first.
+// Work list: (plan, chunk, tile), the plans with the most work per tile first;
+// plans whose own tuning selects the tensor cores are left out of it (they run
+// as their own launches inside the batch's graph).
 int batch_build(das_batch *b) {
+    for (int i = 0; i < b->n; ++i) b->tc[i] = b->plans[i]->tuning.tensor_cores && tc_capable(b->plans[i]);
     const int fb = batch_choose_fb(b);
     if (!batch_fb_supported(is_iq(b->plans[0]), b->plans[0]->storage, fb))
         return fail(DAS_ERR_UNSUPPORTED, "frames_per_thread %d not compiled for batches of this storage", fb);
@@ -1258,6 +1263,7 @@ int batch_build(das_batch *b) {
     for (int oi = 0; oi < b->n; ++oi) {
         const int i = order[oi];
         das_plan *p = b->plans[i];
+        if (b->tc[i]) continue;
         const int nch = (b->frames[i] + fb - 1) / fb;
         int rc = ensure_scratch_frames(p, nch * fb);
         if (rc != DAS_OK) return rc;
@@ -1268,8 +1274,10 @@ int batch_build(das_batch *b) {
     if (items.size() > 0x7fffffff) return fail(DAS_ERR_UNSUPPORTED, "too many work items");
     if (b->items) cudaFree(b->items);
     b->items = nullptr;
-    DAS_CU(cudaMalloc(&b->items, sizeof(int4) * items.size()));
-    DAS_CU(cudaMemcpy(b->items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice));
+    if (!items.empty()) {
+        DAS_CU(cudaMalloc(&b->items, sizeof(int4) * items.size()));
+        DAS_CU(cudaMemcpy(b->items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice));
+    }
     b->n_items = (int)items.size();
     b->fb = fb;
     batch_drop_graph(b);
@@ -1337,7 +1345,8 @@ extern "C" int das_batch_set_tuning(das_batch_t *b, const das_tuning_t *tuning) 
     if (!b || !tuning) return fail(DAS_ERR_INVALID_ARG, "NULL argument");
     if (tuning->frames_per_thread < 0 || tuning->ctas_per_sm < 0 || tuning->staging < 0 || tuning->tensor_cores < 0)
         return fail(DAS_ERR_INVALID_ARG, "negative tuning value");
-    if (tuning->tensor_cores) return fail(DAS_ERR_UNSUPPORTED, "the batched launch runs on the CUDA cores");
+    if (tuning->tensor_cores)
+        return fail(DAS_ERR_UNSUPPORTED, "choose the tensor cores per plan (das_plan_set_tuning), not per batch");
     DeviceGuard guard(b->device);
     if (!guard.ok) return fail(DAS_ERR_CUDA, "cannot select the plan's device");
     b->tuning = *tuning;
@@ -1375,8 +1384,14 @@ extern "C" int das_batch_forward(das_batch_t *b, const void *const *y_dev, void 
         int kernels = 0;
         for (int i = 0; i < b->n && rc == DAS_OK; ++i) {
             das_plan *p = b->plans[i];
-            const int nch = (b->frames[i] + b->fb - 1) / b->fb;
             const long long l0 = p->launches;
+            if (b->tc[i]) {
+                // this plan's tensor-core launches (scales, operand relayout, tcgen05 kernel)
+                rc = forward_tc(p, y_dev[i], x_dev[i], b->frames[i], b->cap);
+                kernels += (int)(p->launches - l0);
+                continue;
+            }
+            const int nch = (b->frames[i] + b->fb - 1) / b->fb;
             const void *z = nullptr;
             rc = stage_channels(p, y_dev[i], b->frames[i], b->fb, nch, 0, b->cap, &z);
             kernels += (int)(p->launches - l0);
@@ -1390,11 +1405,13 @@ extern "C" int das_batch_forward(das_batch_t *b, const void *const *y_dev, void 
             P.items = b->items;
             P.n_items = b->n_items;
             P.counter = b->counter;
-            e = cudaMemsetAsync(b->counter, 0, sizeof(int), b->cap);
-            if (e == cudaSuccess)
-                e = launch_batch(P, b->n, is_iq(b->plans[0]), b->plans[0]->storage, b->fb, b->tuning.ctas_per_sm,
-                                 b->tuning.staging, b->cap);
-            kernels += 1;
+            if (b->n_items > 0) {  // CUDA-core plans: the persistent launch over their work items
+                e = cudaMemsetAsync(b->counter, 0, sizeof(int), b->cap);
+                if (e == cudaSuccess)
+                    e = launch_batch(P, b->n, is_iq(b->plans[0]), b->plans[0]->storage, b->fb,
+                                     b->tuning.ctas_per_sm, b->tuning.staging, b->cap);
+                kernels += 1;
+            }
         }
         cudaGraph_t graph = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(b->cap, &graph);

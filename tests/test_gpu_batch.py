@@ -124,3 +124,30 @@ def test_autotuner_choice_keeps_result(das, tmp_path, monkeypatch):
     batch.close()
     for p in plans:
         p.close()
+
+
+@pytest.mark.parametrize("tc_plans", [(True, False, False), (True, True, True)])
+def test_batch_with_tensor_core_plans(das, oracle, tc_plans):
+    """Plans whose own tuning selects the tensor cores run as their own
+    launches inside the batch's graph, the others in the persistent launch
+    (all three on the tensor cores: no persistent launch at all); every image
+    against the oracle at the 16-bit bar, on capture and on replay."""
+    scenes = three_scenes()
+    frames = [3, 2, 5]
+    ys = [S.random_channels(sc, f, seed=110 + i).cuda() for i, (sc, f) in enumerate(zip(scenes, frames))]
+    plans = [das.Plan.from_scene(sc, storage="f16", max_batch=f) for sc, f in zip(scenes, frames)]
+    for p, tc in zip(plans, tc_plans):
+        p.set_tuning(tensor_cores=tc)
+    batch = das.Batch(plans, frames)
+    n_cc = sum(1 for tc in tc_plans if not tc)
+    for rep in range(2):  # capture, then replay
+        outs = batch.forward(ys)
+        for sc, y, x, p in zip(scenes, ys, outs, plans):
+            assert_parity(x.reshape(x.shape[0], -1).cpu().numpy(), oracle.forward(sc, y.cpu().numpy()), BAR["f16"],
+                          what=f"{sc.name}, tensor cores {p.info()['tc_mma_n'] > 0}")
+            p.check()
+    info = batch.info()
+    assert (info["work_items"] > 0) == (n_cc > 0)
+    batch.close()
+    for p in plans:
+        p.close()
