@@ -132,7 +132,9 @@ typedef struct {
     int frames_per_thread; /* frames accumulated per thread in the forward kernel (0: automatic) */
     int ctas_per_sm;       /* occupancy hint for persistent launches and the tensor-core
                               kernel (0: automatic); on the tensor-core path 2 also limits a
-                              frame chunk to 112 frames so that two CTAs fit an SM */
+                              frame chunk to 112 frames so that two CTAs fit an SM, and 3 or 4
+                              run CTAs of one builder group each with 48 frames per chunk
+                              (automatic: 4 when a chunk holds 48 frames or fewer) */
     int staging;           /* 1: stage each (element, transmit) window of sample rows in shared
                               memory with bulk asynchronous copies; 0: read rows straight from
                               global memory (default) */

@@ -158,7 +158,7 @@ def tune_plan(plan: Plan, y, out, fbs: Optional[Iterable[int]] = None, staging=(
                     continue
                 results.append(dict(cfg, ms=_time(lambda: plan.forward(y, out), reps, warmup)))
     if True in tuple(tensor_cores) and plan.iq and plan.storage in ("f16", "bf16"):
-        for ctas in (1, 2):
+        for ctas in (1, 2, 3, 4):
             cfg = {"tensor_cores": True, "frames_per_thread": 0, "staging": False, "load_width": 0,
                    "ctas_per_sm": ctas}
             try:

@@ -936,18 +936,23 @@ cudaError_t launch_tc(const TcArgs &args, int bf16, const void *z, int nch, int 
     if (((uintptr_t)z & 15u) != 0) return cudaErrorInvalidValue;
     PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
     if (!encode) return cudaErrorNotSupported;
-    // CTAs per SM: two while the accumulator leaves room for two W stages in
-    // half of the tensor memory, else one (registers allow at most two).
-    int per_sm = ctas_per_sm > 0 ? ctas_per_sm : 2;
-    if (per_sm > 2) per_sm = 2;
+    // CTAs per SM: automatically four CTAs of one builder group each while the
+    // accumulator and two W stages fit 128 tensor-memory columns (N <= 96, up
+    // to 48 frames), so that four MMA-issuing threads per SM overlap their
+    // per-sub-item hand-offs (paper workload, 20 frames: 119.3 ms against
+    // 166.7 ms with two CTAs); else two while they fit half of the tensor
+    // memory, else one.  Three, or the others, on request.
+    int per_sm = ctas_per_sm > 0 ? ctas_per_sm : (A.n + 2 * TC_ACOLS <= 128 ? 4 : 2);
+    if (per_sm > 4) per_sm = 4;
+    if (per_sm >= 3 && A.n + 2 * TC_ACOLS > 128) per_sm = 2;
     if (per_sm == 2 && A.n + 2 * TC_ACOLS > 256) per_sm = 1;
-    A.ncols = 512 / per_sm;
+    A.ncols = per_sm >= 3 ? 128 : 512 / per_sm;
     int sa = 1;
     while (2 * sa <= TC_MAX_SA && A.n + 2 * sa * TC_ACOLS <= A.ncols) sa *= 2;
     if (sa < 2) return cudaErrorInvalidConfiguration;
     A.sa = sa;
     const bool has_w = A.w_tx != nullptr;
-    const int G = per_sm >= 2 ? 2 : 4;
+    const int G = per_sm >= 3 ? 1 : per_sm == 2 ? 2 : 4;
     const int eb = G * TILE_N;
     // a list holds every sub-item of a block when no item needs two windows
     long long cap = (long long)eb * A.Q;
@@ -981,7 +986,13 @@ cudaError_t launch_tc(const TcArgs &args, int bf16, const void *z, int nch, int 
                               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-    if (per_sm >= 2) {
+    if (per_sm == 4) {
+        return bf16 ? launch_tc_t<true, 1, 4>(map, A, smem, nch, s) : launch_tc_t<false, 1, 4>(map, A, smem, nch, s);
+    }
+    if (per_sm == 3) {
+        return bf16 ? launch_tc_t<true, 1, 3>(map, A, smem, nch, s) : launch_tc_t<false, 1, 3>(map, A, smem, nch, s);
+    }
+    if (per_sm == 2) {
         return bf16 ? launch_tc_t<true, 2, 2>(map, A, smem, nch, s) : launch_tc_t<false, 2, 2>(map, A, smem, nch, s);
     }
     return bf16 ? launch_tc_t<true, 4, 1>(map, A, smem, nch, s) : launch_tc_t<false, 4, 1>(map, A, smem, nch, s);

@@ -56,9 +56,10 @@ cudaError_t launch_tc(const TcArgs &args, int bf16, const void *z, int nch, int 
 // MMA width and frames per chunk of the tensor-core path for a call of B
 // frames, at most max_bc (<= 128) frames per chunk.
 void tc_shape(int B, int max_bc, int &bc, int &nch, int &n);
-// Frames per chunk: 128 (N up to 256, one CTA per SM), or 112 when two CTAs
-// per SM are asked for (N <= 224 leaves room for the weight stages).
-inline int tc_max_frames(int ctas_per_sm) { return ctas_per_sm == 2 ? 112 : 128; }
+// Frames per chunk: 128 (N up to 256, one CTA per SM), 112 when two CTAs per
+// SM are asked for (N <= 224 leaves room for the weight stages), 48 with three
+// or four (N <= 96 in 128 tensor-memory columns).
+inline int tc_max_frames(int ctas_per_sm) { return ctas_per_sm >= 3 ? 48 : ctas_per_sm == 2 ? 112 : 128; }
 cudaError_t launch_scale(const void *y, float *scale, float *inv_scale, int iq, int store, int B, int QM, int K,
                          cudaStream_t s);
 

@@ -61,11 +61,14 @@ def test_ragged_tiles_and_transmit_kinds(das, oracle, case, B):
     assert_parity(x, oracle.forward(sc, y.numpy()), TOL["f16"], what=f"ragged case {case}, {B} frames")
 
 
-@pytest.mark.parametrize("B,ctas", [(16, 0), (128, 0), (130, 0), (128, 2), (130, 2), (112, 2)])
+@pytest.mark.parametrize("B,ctas", [(16, 0), (128, 0), (130, 0), (128, 2), (130, 2), (112, 2), (20, 3), (48, 4),
+                                    (100, 3)])
 def test_mma_widths_and_frame_chunks(das, oracle, B, ctas):
     """N = 32 and the largest N = 256 (128 frames), and two frame chunks (130
     frames); with two CTAs per SM at most 112 frames per chunk (128 frames:
-    two chunks of 64, N = 128; 112 frames: one chunk, N = 224)."""
+    two chunks of 64, N = 128; 112 frames: one chunk, N = 224); with three or
+    four CTAs per SM (one builder group each) at most 48 frames per chunk
+    (100 frames: three chunks of 34, N = 80)."""
     sc = ragged_scene(*RAGGED[0])
     y = S.random_channels(sc, B, seed=B)
     x = tc_forward(das, sc, y, ctas_per_sm=ctas).cpu().numpy()
