@@ -215,6 +215,31 @@ __global__ void __launch_bounds__(256) relayout_kernel(const void *__restrict__ 
             tile[ty + 8 * i][tx] = v;
         }
         __syncthreads();
+        if constexpr (IQ && ST == ST_F32) {
+            if (col && fb % 2 == 0) {
+                // column order, float32 IQ: one thread writes a whole 16-byte piece
+                // (re_2p, re_2p+1, im_2p, im_2p+1) of frames 2p, 2p + 1 of row k;
+                // lanes run along k, so a warp writes 512 contiguous bytes
+                for (int i = threadIdx.x; i < 16 * 32; i += 256) {
+                    const int kl = i & 31, pp = i >> 5;
+                    const int k = k0 + kl, b = bc + 2 * pp;  // bc and fb even: a pair never straddles a chunk
+                    if (k < K && b < Bs) {
+                        float2 v0 = tile[2 * pp][kl], v1 = tile[2 * pp + 1][kl];
+                        if (rot) {
+                            const float2 r = rot[k];
+                            v0 = cmul(v0, r);
+                            v1 = cmul(v1, r);
+                        }
+                        const int c = b / fb, j = b - c * fb;
+                        unsigned char *blk = zb + ((size_t)c * QM + qm) * (size_t)K * RB;
+                        *reinterpret_cast<float4 *>(blk + row_byte(k, 16 * (j >> 1), K, RB, true)) =
+                            make_float4(v0.x * s, v1.x * s, v0.y * s, v1.y * s);
+                    }
+                }
+                __syncthreads();
+                continue;
+            }
+        }
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int kl = ty + 8 * i, k = k0 + kl, b = bc + tx;
