@@ -13,7 +13,7 @@ cudaError_t launch_tile_e5m2(const TileArgs &A, int mode, int iq, int fb, int n_
 bool tile_fb_supported(int mode, int iq, int store, int fb) {
     (void)iq;
     if (mode == MODE_COUNT) return fb == 1;
-    if (store == ST_F32) return fb == 1 || fb == 2 || fb == 4 || fb == 8 || fb == 12 || fb == 16 || fb == 20;
+    if (store == ST_F32) return fb == 1 || fb == 2 || fb == 4 || fb == 8 || fb == 10 || fb == 12 || fb == 16 || fb == 20;
     if (mode != MODE_FWD) return false;
     if ((store == ST_E4M3 || store == ST_E5M2) && !iq) return false;
     return fb == 1 || fb == 2 || fb == 4 || fb == 8 || fb == 12 || fb == 16 || fb == 20 || fb == 24;

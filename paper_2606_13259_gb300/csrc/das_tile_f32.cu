@@ -19,6 +19,7 @@ cudaError_t launch_tile_f32(const TileArgs &A, int mode, int iq, int fb, int n_c
         DAS_F32_CASE(2)
         DAS_F32_CASE(4)
         DAS_F32_CASE(8)
+        DAS_F32_CASE(10)
         DAS_F32_CASE(12)
         DAS_F32_CASE(16)
         DAS_F32_CASE(20)

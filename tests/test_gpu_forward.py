@@ -89,7 +89,7 @@ def test_ragged_tiles_transmit_kinds_and_batches(das, oracle, case, B):
     assert_parity(x, ref, TOL_F32, what=f"ragged case {case}, {B} frames")
 
 
-@pytest.mark.parametrize("fb", [1, 2, 4, 8, 12, 16, 20])
+@pytest.mark.parametrize("fb", [1, 2, 4, 8, 10, 12, 16, 20])
 def test_frames_per_thread_variants(das, oracle, fb):
     """Every compiled frames-per-thread width gives the same image (padding of
     the last frame chunk included)."""
