@@ -202,12 +202,18 @@ __global__ void __launch_bounds__(ADJ_THREADS, 2) adjoint_kernel(const AdjArgs A
                 float a0[FB * C], a1[FB * C];
 #pragma unroll
                 for (int i = 0; i < FB * C; ++i) a0[i] = a1[i] = 0.f;
+                // transmit rests of the line's 8 voxels: tile lanes vbase + 0..3 (x = 0..3)
+                // and vbase + 8..11 (x = 4..7), two aligned 16-byte loads
+                const int vbase = ((ly & 1) << 2) | (((ly >> 1) << 1) << 3) | (lz << 5);
+                const float4 t03 = __ldg(reinterpret_cast<const float4 *>(A.tx_t + tq * TILE_N + vbase));
+                const float4 t47 = __ldg(reinterpret_cast<const float4 *>(A.tx_t + tq * TILE_N + vbase + 8));
+                const float tl[TILE_X] = {t03.x, t03.y, t03.z, t03.w, t47.x, t47.y, t47.z, t47.w};
 #pragma unroll
                 for (int x = 0; x < TILE_X; ++x) {
                     if (!((live >> x) & 1u)) continue;
                     // tile lane of voxel (x, ly, lz) (inverse of lane_offset)
                     const int vl = ((x & 3) | ((ly & 1) << 2)) | (((x >> 2) | ((ly >> 1) << 1)) << 3) | (lz << 5);
-                    const float f = r[x] + __ldg(A.tx_t + tq * TILE_N + vl);
+                    const float f = r[x] + tl[x];
                     const float fl = floorf(f);
                     const float al = f - fl;
                     const int k = kb + (int)fl;
