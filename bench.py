@@ -669,7 +669,8 @@ def main():
         "config": {"workload": sc.name, "frames_per_step": F, "voxels": sc.N, "elements": sc.M,
                    "transmits": sc.Q, "samples": sc.K, "storage": args.storage,
                    "l2": f"inputs {y.numel() * 8 / 1e9:.1f} GB > 129 MB L2, no flush", "per_rank_frames": F,
-                   "staging": args.staging, "load_width": args.load_width or 128,
+                   "staging": args.staging,
+                   "row_loads": f"row order, {args.load_width}-bit" if args.load_width else "column order, 128-bit",
                    "frames_per_thread": args.fb or "auto", "tensor_cores": bool(args.tensor_cores),
                    "voxels_per_thread": args.vpt or "auto",
                    **({"tc_chain": args.tc_chain or "auto"} if args.tensor_cores else {})},

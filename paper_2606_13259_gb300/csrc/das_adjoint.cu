@@ -35,7 +35,7 @@ struct AdjTileRec {
     float rf;              // fractional part of the reference delay
     int rb;                // integer part
     int tile;
-    int pad;
+    int inside;            // 1: every row the tile can reach lies in this CTA's band
 };
 
 template <bool IQ, int FB>
@@ -110,6 +110,7 @@ __global__ void __launch_bounds__(ADJ_THREADS, 2) adjoint_kernel(const AdjArgs A
                 const int2 sp = __ldg(A.tx_span + t);
                 const int klo = sp.x + rbf - A.aRi, khi = sp.y + rbf + A.aRi;
                 cand = klo < R1 && khi + 1 >= R0;
+                rec.inside = (klo >= R0 && khi + 1 < R1) ? 1 : 0;
             }
             if (cand) {
                 const double D0 = sqrt(Gx * Gx + Gy * Gy + Gz * Gz);
@@ -119,7 +120,6 @@ __global__ void __launch_bounds__(ADJ_THREADS, 2) adjoint_kernel(const AdjArgs A
                 rec.rf = (float)(Rd - Rf);
                 rec.rb = (int)Rf;
                 rec.tile = (int)t;
-                rec.pad = 0;
             }
         }
         const unsigned bal = __ballot_sync(0xffffffffu, cand);
@@ -192,9 +192,10 @@ __global__ void __launch_bounds__(ADJ_THREADS, 2) adjoint_kernel(const AdjArgs A
                 const int q = q0 + qq;
                 const size_t tq = (size_t)tile * A.Q + q;
                 const int kb = __ldg(A.tx_tb + tq) + R.rb;
-                // this transmit's rows of the tile against the band
-                if (kb + (int)floorf(__ldg(A.tx_tmin + tq)) - A.aRi >= R1 ||
-                    kb + (int)floorf(__ldg(A.tx_tmax + tq)) + A.aRi + 2 < R0)
+                // this transmit's rows of the tile against the band (not needed when
+                // every row the tile can reach lies in the band)
+                if (!R.inside && (kb + (int)floorf(__ldg(A.tx_tmin + tq)) - A.aRi >= R1 ||
+                                  kb + (int)floorf(__ldg(A.tx_tmax + tq)) + A.aRi + 2 < R0))
                     continue;
                 float *const arow = acc + (size_t)qq * L * FB * C;  // row k at arow + (k - R0) FB C
                 // running rows kc and kc + 1 (kc = -4: none yet)

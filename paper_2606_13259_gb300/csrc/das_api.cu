@@ -336,8 +336,9 @@ int ensure_tc_scratch(das_plan *p) {
 }
 
 // Forward pass on the tensor cores: per-(q, m) scales, the operand relayout,
-// then the tcgen05 kernel (das_tc.cu).
-int forward_tc(das_plan *p, const void *y, void *x, int B, cudaStream_t s) {
+// then the tcgen05 kernel (das_tc.cu).  `timing`: record the plan's kernel
+// events when they are enabled (not inside a batch's graph capture).
+int forward_tc(das_plan *p, const void *y, void *x, int B, cudaStream_t s, bool timing = true) {
     int bc, nch, n;
     tc_shape(B, tc_max_frames(p->tuning.ctas_per_sm), bc, nch, n);
     const int QM = p->Q * p->M;
@@ -381,7 +382,7 @@ int forward_tc(das_plan *p, const void *y, void *x, int B, cudaStream_t s) {
     A.chain = p->tuning.tc_chain > 0 ? p->tuning.tc_chain
               : (p->tuning.tc_chain == 0 && p->Q >= TC_CHAIN_MIN_TX ? TC_CHAIN_DEFAULT : 0);
     p->tc_n = n;
-    const bool timed = p->ev_used < (int)p->ev_start.size();
+    const bool timed = timing && p->ev_used < (int)p->ev_start.size();
     if (timed) DAS_CU(cudaEventRecord(p->ev_start[p->ev_used], s));
     DAS_CU(launch_tc(A, bf16 ? 1 : 0, p->z_tc, nch, p->tuning.ctas_per_sm, s));
     p->launches += 1;
@@ -1387,7 +1388,7 @@ extern "C" int das_batch_forward(das_batch_t *b, const void *const *y_dev, void 
             const long long l0 = p->launches;
             if (b->tc[i]) {
                 // this plan's tensor-core launches (scales, operand relayout, tcgen05 kernel)
-                rc = forward_tc(p, y_dev[i], x_dev[i], b->frames[i], b->cap);
+                rc = forward_tc(p, y_dev[i], x_dev[i], b->frames[i], b->cap, false);
                 kernels += (int)(p->launches - l0);
                 continue;
             }
