@@ -160,6 +160,13 @@ typedef struct {
                               rows for their four taps; 0 (default) or 1: one voxel per thread */
     int adjoint_rows;      /* das_adjoint: sample rows per CTA band (0: automatic); each CTA
                               accumulates one band of one element's rows in shared memory */
+    int host_io;           /* das_forward_host / das_forward_host_many: 0 or 1 (default) copy the
+                              batches through device staging buffers; 2: the kernels read the
+                              channel data from, and write the image to, the caller's host memory
+                              directly over the CPU-GPU link, no copy and no staging buffer: the
+                              buffers must be page-locked (das_host_alloc, cudaHostAlloc,
+                              cudaHostRegister) or, on systems where the GPU uses the host's page
+                              tables, any host memory; others give DAS_ERR_INVALID_ARG */
 } das_tuning_t;
 
 /* Build a plan (Sec. 2 problem statement: grid, receivers, observations, c).
@@ -191,7 +198,8 @@ int das_forward(das_plan_t *plan, const void *y_dev, void *x_dev, int batch, das
 
 /* das_forward with host buffers: copies y_host to the device, runs the
  * forward pass and copies the image back into x_host, then synchronises the
- * stream.  Uses device staging buffers, copy streams and events the plan
+ * stream (with das_tuning_t.host_io = 2 the kernels read y_host and write
+ * x_host directly instead, no copies: page-locked buffers only).  Uses device staging buffers, copy streams and events the plan
  * creates on first use (so the first call allocates).  Each copy is split
  * into up to 16 pieces on the plan's own copy streams, ordered with the work
  * on `stream`.  Pinned host memory is needed for full speed; memory from

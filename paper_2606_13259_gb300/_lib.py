@@ -57,7 +57,7 @@ class PlanInfo(C.Structure):
 class Tuning(C.Structure):
     _fields_ = [("frames_per_thread", C.c_int), ("ctas_per_sm", C.c_int), ("staging", C.c_int),
                 ("load_width", C.c_int), ("tensor_cores", C.c_int), ("tc_chain", C.c_int),
-                ("voxels_per_thread", C.c_int), ("adjoint_rows", C.c_int)]
+                ("voxels_per_thread", C.c_int), ("adjoint_rows", C.c_int), ("host_io", C.c_int)]
 
 
 class DASError(RuntimeError):

@@ -735,6 +735,7 @@ int das_plan_set_tuning(das_plan_t *plan, const das_tuning_t *tuning) {
     if (tuning->voxels_per_thread < 0 || tuning->voxels_per_thread > 2)
         return fail(DAS_ERR_INVALID_ARG, "voxels_per_thread must be 0, 1 or 2");
     if (tuning->adjoint_rows < 0) return fail(DAS_ERR_INVALID_ARG, "adjoint_rows must be >= 0");
+    if (tuning->host_io < 0 || tuning->host_io > 2) return fail(DAS_ERR_INVALID_ARG, "host_io must be 0, 1 or 2");
     if (tuning->tensor_cores && !tc_capable(plan))
         return fail(DAS_ERR_UNSUPPORTED, "the tensor-core path takes IQ data stored as f16 or bf16");
     if (tuning->load_width != 0 && tuning->load_width != 128 && tuning->load_width != 256)
@@ -830,6 +831,44 @@ static int ensure_host_io(das_plan *p, int slots) {
     return DAS_OK;
 }
 
+// Device addresses of a page-locked host range [p, p + bytes) (host_io = 2):
+// both ends must be registered and map to one contiguous device range.
+static int host_device_ptr(const void *p, size_t bytes, void **dev) {
+    void *a = nullptr, *b = nullptr;
+    if (cudaHostGetDevicePointer(&a, const_cast<void *>(p), 0) != cudaSuccess ||
+        cudaHostGetDevicePointer(&b, (char *)const_cast<void *>(p) + (bytes - 1), 0) != cudaSuccess ||
+        (char *)b - (char *)a != (ptrdiff_t)(bytes - 1)) {
+        cudaGetLastError();
+        return fail(DAS_ERR_INVALID_ARG,
+                    "host_io = 2 reads and writes host memory from the GPU: the buffers must be memory the "
+                    "GPU can address (page-locked: das_host_alloc, cudaHostAlloc or cudaHostRegister)");
+    }
+    *dev = a;
+    return DAS_OK;
+}
+
+// host_io = 2: the forward pass of each batch on the device addresses of the
+// caller's page-locked host buffers (the relayout reads the channel data over
+// the CPU-GPU link, the tile kernel writes the image there), then one sync.
+static int forward_host_direct(das_plan *plan, const void *const *y_host, void *const *x_host, int n_batches,
+                               int batch, cudaStream_t s) {
+    const size_t yb = (size_t)batch * plan->Q * plan->M * plan->K * sample_bytes_public(plan);
+    const size_t xb = (size_t)batch * plan->g.n_voxels * sample_bytes_public(plan);
+    std::vector<void *> yd(n_batches), xd(n_batches);
+    int rc;
+    for (int i = 0; i < n_batches; ++i)
+        if ((rc = host_device_ptr(y_host[i], yb, &yd[i])) != DAS_OK ||
+            (rc = host_device_ptr(x_host[i], xb, &xd[i])) != DAS_OK)
+            return rc;
+    for (int i = 0; i < n_batches; ++i)
+        if ((rc = das_forward(plan, yd[i], xd[i], batch, (das_stream_t)s)) != DAS_OK) {
+            cudaStreamSynchronize(s);  // earlier batches still use the caller's buffers
+            return rc;
+        }
+    DAS_CU(cudaStreamSynchronize(s));
+    return DAS_OK;
+}
+
 int das_forward_host(das_plan_t *plan, const void *y_host, void *x_host, int batch, das_stream_t stream) {
     g_err[0] = 0;
     int rc = check_call(plan, y_host, x_host, batch);
@@ -837,6 +876,7 @@ int das_forward_host(das_plan_t *plan, const void *y_host, void *x_host, int bat
     DeviceGuard guard(plan->device);
     if (!guard.ok) return fail(DAS_ERR_CUDA, "cannot select the plan's device");
     cudaStream_t s = (cudaStream_t)stream;
+    if (plan->tuning.host_io == 2) return forward_host_direct(plan, &y_host, &x_host, 1, batch, s);
     if ((rc = ensure_host_io(plan, 1)) != DAS_OK) return rc;
     const size_t yb = (size_t)batch * plan->Q * plan->M * plan->K * sample_bytes_public(plan);
     const size_t xb = (size_t)batch * plan->g.n_voxels * sample_bytes_public(plan);
@@ -927,6 +967,7 @@ int das_forward_host_many(das_plan_t *plan, const void *const *y_host, void *con
     DeviceGuard guard(plan->device);
     if (!guard.ok) return fail(DAS_ERR_CUDA, "cannot select the plan's device");
     cudaStream_t s = (cudaStream_t)stream;
+    if (plan->tuning.host_io == 2) return forward_host_direct(plan, y_host, x_host, n_batches, batch, s);
     if ((rc = ensure_host_io(plan, 2)) != DAS_OK) return rc;
     rc = forward_host_many_run(plan, y_host, x_host, n_batches, batch, s);
     if (rc != DAS_OK) {

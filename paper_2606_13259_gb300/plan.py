@@ -125,15 +125,18 @@ class Plan:
 
     def set_tuning(self, frames_per_thread: int = 0, ctas_per_sm: int = 0, staging: bool = False,
                    load_width: int = 0, tensor_cores: bool = False, tc_chain: int = 0,
-                   voxels_per_thread: int = 0, adjoint_rows: int = 0) -> None:
+                   voxels_per_thread: int = 0, adjoint_rows: int = 0, host_io: int = 0) -> None:
         """Kernel shape of the forward pass; tensor_cores selects the tcgen05
         contraction (IQ data with f16 / bf16 storage), tc_chain the MMA
         sub-items per tensor-memory accumulation chain (0: automatic, 1024
         with 4 or more transmits; -1: one chain per tile), voxels_per_thread
         the float32 IQ kernel with one (the default) or two voxels per thread,
-        adjoint_rows the sample rows per CTA of the adjoint (0: automatic)."""
+        adjoint_rows the sample rows per CTA of the adjoint (0: automatic),
+        host_io how the host calls move data (0 / 1 copies, 2 the kernels
+        read and write page-locked host memory directly)."""
         t = L.Tuning(int(frames_per_thread), int(ctas_per_sm), 1 if staging else 0, int(load_width),
-                     1 if tensor_cores else 0, int(tc_chain), int(voxels_per_thread), int(adjoint_rows))
+                     1 if tensor_cores else 0, int(tc_chain), int(voxels_per_thread), int(adjoint_rows),
+                     int(host_io))
         L.check(self._lib.das_plan_set_tuning(self._h, C.byref(t)))
 
     def check(self, stream=None) -> None:
@@ -356,7 +359,7 @@ class Batch:
             pass
 
     def set_tuning(self, frames_per_thread: int = 0, ctas_per_sm: int = 0, staging: bool = False) -> None:
-        t = L.Tuning(int(frames_per_thread), int(ctas_per_sm), 1 if staging else 0, 0, 0, 0, 0, 0)
+        t = L.Tuning(int(frames_per_thread), int(ctas_per_sm), 1 if staging else 0, 0, 0, 0, 0, 0, 0)
         L.check(self._lib.das_batch_set_tuning(self._h, C.byref(t)))
 
     def info(self) -> dict:

@@ -288,6 +288,43 @@ def test_forward_host_matches_device_call(das, kind):
     assert torch.equal(xh, ref)
 
 
+@pytest.mark.parametrize("kind", ["huge_pages", "pinned"])
+def test_direct_host_io_matches_device_call(das, kind):
+    """host_io = 2: the kernels read the channel data from page-locked host
+    memory and write the image there directly (no copies, no staging), for
+    one call and for a sequence; bit-identical to the device call.  A pageable
+    buffer is either refused before any launch or, where the GPU reaches host
+    memory through the host's page tables (this platform), read directly with
+    the same result."""
+    sc = ragged_scene(*RAGGED[0])
+    B = 5
+    ys = [S.random_channels(sc, B, seed=140 + i) for i in range(3)]
+    plan = das.Plan.from_scene(sc, max_batch=B)
+    refs = [plan.forward(y.cuda()).cpu() for y in ys]
+    plan.set_tuning(host_io=2)
+    alloc = (lambda shape, dt: das.host_empty(shape, dt)) if kind == "huge_pages" else \
+        (lambda shape, dt: torch.empty(shape, dtype=dt).pin_memory())
+    yh = [alloc(y.shape, y.dtype) for y in ys]
+    for h, y in zip(yh, ys):
+        h.copy_(y)
+    xh = alloc(refs[0].shape, refs[0].dtype)
+    plan.forward_host(yh[0], xh)
+    assert torch.equal(xh, refs[0])
+    outs = plan.forward_host_many(yh)
+    for o, r in zip(outs, refs):
+        assert torch.equal(o, r)
+    pageable = torch.empty(ys[0].shape, dtype=ys[0].dtype)
+    pageable.copy_(ys[0])
+    xh.zero_()
+    try:
+        plan.forward_host(pageable, xh)
+        assert torch.equal(xh, refs[0])
+    except das.DASError:
+        pass
+    plan.check()
+    plan.close()
+
+
 @pytest.mark.parametrize("n_batches,B", [(1, 5), (2, 5), (5, 3)])
 def test_forward_host_many_matches_device_calls(das, n_batches, B):
     """A sequence of host batches with copies overlapped with the forward
