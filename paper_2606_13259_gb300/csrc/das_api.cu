@@ -360,6 +360,8 @@ int forward_tc(das_plan *p, const void *y, void *x, int B, cudaStream_t s, bool 
     A.bc = bc;
     A.n = n;
     fill_common(p, A.a, A.ad, A.theta, A.hr, A.hi, A.thr, A.tile_radius);
+    A.er = (float)cos(2.0 * M_PI * p->f_demod / p->fs);
+    A.ei = (float)-sin(2.0 * M_PI * p->f_demod / p->fs);
     A.ahx = (float)(A.ad * 0.5 * (TILE_X - 1) * p->g.sx);
     A.ahy = (float)(A.ad * 0.5 * (TILE_Y - 1) * p->g.sy);
     A.ahz = (float)(A.ad * 0.5 * (TILE_Z - 1) * p->g.sz);

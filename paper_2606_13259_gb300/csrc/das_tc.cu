@@ -633,10 +633,12 @@ __global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_co
                     const int u = k - ent.x;
                     float w = has_w ? s_w[q * TILE_N + vl] : 1.f;
                     w *= s_lw[e];
+                    // e^{i th a} directly (th a in [0, th]; the weights are rounded to
+                    // 16 bits), and e^{-i th (1-a)} = e^{i th a} e^{-i th}
                     float sn, cs;
-                    __sincosf(A.theta * (al - 0.5f), &sn, &cs);
-                    const float uhr = cs * A.hr - sn * A.hi, uhi = cs * A.hi + sn * A.hr;  // e^{i th a}
-                    const float ubr = cs * A.hr + sn * A.hi, ubi = sn * A.hr - cs * A.hi;  // e^{-i th (1-a)}
+                    __sincosf(A.theta * al, &sn, &cs);
+                    const float uhr = cs, uhi = sn;
+                    const float ubr = cs * A.er - sn * A.ei, ubi = cs * A.ei + sn * A.er;
                     const float w0 = w * (1.f - al), w1 = w * al;
                     const uint32_t pr = pack2<BF16>(w0 * uhr, w1 * ubr);  // (Wr[u], Wr[u+1])
                     const uint32_t pi = pack2<BF16>(w0 * uhi, w1 * ubi);  // (Wi[u], Wi[u+1])

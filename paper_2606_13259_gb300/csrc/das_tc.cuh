@@ -27,6 +27,7 @@ struct TcArgs {
     float a;          // fs / c
     double ad;
     float theta, hr, hi, thr, tile_radius;
+    float er, ei;         // e^{-i theta}
     float ahx, ahy, ahz;  // a times the half extents of the tile's voxel-centre box
     float aR;             // a times the tile radius
     float aR2h;           // a R^2 / 2
