@@ -940,36 +940,54 @@ cudaError_t launch_tc(const TcArgs &args, int bf16, const void *z, int nch, int 
     if (!encode) return cudaErrorNotSupported;
     // CTAs per SM: automatically four CTAs of one builder group each while the
     // accumulator and two W stages fit 128 tensor-memory columns (N <= 96, up
-    // to 48 frames), so that four MMA-issuing threads per SM overlap their
+    // to 48 frames) and the CTA's tables and window stages fit a quarter of the
+    // shared memory, so that four MMA-issuing threads per SM overlap their
     // per-sub-item hand-offs (paper workload, 20 frames: 119.3 ms against
     // 166.7 ms with two CTAs); else two while they fit half of the tensor
-    // memory, else one.  Three, or the others, on request.
-    int per_sm = ctas_per_sm > 0 ? ctas_per_sm : (A.n + 2 * TC_ACOLS <= 128 ? 4 : 2);
-    if (per_sm > 4) per_sm = 4;
-    if (per_sm >= 3 && A.n + 2 * TC_ACOLS > 128) per_sm = 2;
-    if (per_sm == 2 && A.n + 2 * TC_ACOLS > 256) per_sm = 1;
-    A.ncols = per_sm >= 3 ? 128 : 512 / per_sm;
-    int sa = 1;
-    while (2 * sa <= TC_MAX_SA && A.n + 2 * sa * TC_ACOLS <= A.ncols) sa *= 2;
-    if (sa < 2) return cudaErrorInvalidConfiguration;
-    A.sa = sa;
+    // memory and of the shared memory, else one.  Three, or the others, on
+    // request (refused when they do not fit).
     const bool has_w = A.w_tx != nullptr;
-    const int G = per_sm >= 3 ? 1 : per_sm == 2 ? 2 : 4;
-    const int eb = G * TILE_N;
-    // a list holds every sub-item of a block when no item needs two windows
-    long long cap = (long long)eb * A.Q;
-    if (cap < 256) cap = 256;
-    if (cap > TC_LIST_MAX) cap = TC_LIST_MAX;
-    // a chain ends at a list end: lists no longer than a chain keep chains short
-    if (A.chain > 0 && cap > A.chain) cap = A.chain < 256 ? 256 : A.chain;
-    A.list_cap = (int)cap;
-    const size_t budget = (size_t)(227 * 1024) / per_sm - 1024;  // per-CTA share incl. the runtime's reserve
-    const size_t fixed = tc_smem_layout(0, A.n, A.Q, has_w, eb, A.list_cap).total;
-    const size_t stage = (size_t)64 * A.n;
-    int sbv = fixed < budget ? (int)((budget - fixed) / stage) : 0;
-    if (sbv > TC_MAX_SB) sbv = TC_MAX_SB;
-    sbv -= sbv % TC_PRODUCERS;
-    if (sbv < TC_PRODUCERS) return cudaErrorInvalidConfiguration;
+    int G = 0, eb = 0, sbv = 0;
+    // Fills the launch shape for `ps` CTAs per SM; false when it does not fit.
+    auto configure = [&](int ps) -> bool {
+        if (ps >= 3 && A.n + 2 * TC_ACOLS > 128) return false;
+        if (ps == 2 && A.n + 2 * TC_ACOLS > 256) return false;
+        A.ncols = ps >= 3 ? 128 : 512 / ps;
+        int sa = 1;
+        while (2 * sa <= TC_MAX_SA && A.n + 2 * sa * TC_ACOLS <= A.ncols) sa *= 2;
+        if (sa < 2) return false;
+        A.sa = sa;
+        G = ps >= 3 ? 1 : ps == 2 ? 2 : 4;
+        eb = G * TILE_N;
+        // a list holds every sub-item of a block when no item needs two windows
+        long long cap = (long long)eb * A.Q;
+        if (cap < 256) cap = 256;
+        if (cap > TC_LIST_MAX) cap = TC_LIST_MAX;
+        // a chain ends at a list end: lists no longer than a chain keep chains short
+        if (A.chain > 0 && cap > A.chain) cap = A.chain < 256 ? 256 : A.chain;
+        A.list_cap = (int)cap;
+        const size_t budget = (size_t)(227 * 1024) / ps - 1024;  // per-CTA share incl. the runtime's reserve
+        const size_t fixed = tc_smem_layout(0, A.n, A.Q, has_w, eb, A.list_cap).total;
+        const size_t stage = (size_t)64 * A.n;
+        sbv = fixed < budget ? (int)((budget - fixed) / stage) : 0;
+        if (sbv > TC_MAX_SB) sbv = TC_MAX_SB;
+        sbv -= sbv % TC_PRODUCERS;
+        return sbv >= TC_PRODUCERS;
+    };
+    int per_sm = 0;
+    if (ctas_per_sm > 0) {
+        per_sm = ctas_per_sm > 4 ? 4 : ctas_per_sm;
+        if (!configure(per_sm)) {  // keep the former fallback of an explicit request to fewer CTAs
+            if (per_sm >= 3 && configure(2)) per_sm = 2;
+            else if (per_sm >= 2 && configure(1)) per_sm = 1;
+            else return cudaErrorInvalidConfiguration;
+        }
+    } else {
+        const int tries[3] = {4, 2, 1};
+        for (int ps : tries)
+            if (configure(ps)) { per_sm = ps; break; }
+        if (per_sm == 0) return cudaErrorInvalidConfiguration;
+    }
     A.sb = sbv;
     const size_t smem = tc_smem_layout(sbv, A.n, A.Q, has_w, eb, A.list_cap).total;
 

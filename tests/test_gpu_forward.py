@@ -391,6 +391,32 @@ def test_degenerate_shapes(das, oracle, name, tc):
 
 
 @pytest.mark.parametrize("tc", [False, True])
+def test_most_transmits_a_plan_takes(das, oracle, tc):
+    """128 transmits (the most a plan takes; a mix of diverging waves, plane
+    waves and none) on a ragged grid: shared-memory tables of 128 x 128
+    transmit rests per tile, and on the tensor cores lists of 16384 pairs per
+    element block, cut at 4096 sub-items."""
+    sc = S.scene_tiny(iq=True, n=(11, 6, 5), elems=(4, 3), n_tx=128, f_number=1.0, K=96)
+    kinds = np.array([(q % 3) for q in range(128)], np.int32)
+    vec = sc.tx_vec.copy()
+    for q in range(128):
+        if kinds[q] == S.TX_PLANE:
+            a = 0.3 * np.sin(q)
+            vec[q] = [np.sin(a), 0.0, np.cos(a)]
+        elif kinds[q] == S.TX_NONE:
+            vec[q] = [0.0, 0.0, 0.0]
+    sc = sc.with_(tx_kind=kinds, tx_vec=vec)
+    y = S.random_channels(sc, 3, seed=150)
+    plan = das.Plan.from_scene(sc, storage="f16" if tc else "f32", max_batch=3)
+    if tc:
+        plan.set_tuning(tensor_cores=True)
+    x = plan.forward(y.cuda()).cpu().numpy().reshape(3, -1)
+    plan.check()
+    plan.close()
+    assert_parity(x, oracle.forward(sc, y.numpy()), BAR["f16"] if tc else TOL_F32, what="128 transmits")
+
+
+@pytest.mark.parametrize("tc", [False, True])
 def test_no_voxel_inside_any_aperture(das, oracle, tc):
     """Voxels at the depth of the array (z = 0 plane), f-number 1: every term
     is outside the aperture and the image is exactly zero."""
