@@ -64,8 +64,9 @@ def _time(fn, reps: int, warmup: int) -> float:
 
 
 def _set_plan_tc(batch: Batch, flags) -> None:
+    """Each plan on or off the tensor cores, its other settings kept."""
     for p, on in zip(batch.plans, flags):
-        p.set_tuning(tensor_cores=bool(on))
+        p.set_tuning(**dict(p.tuning(), tensor_cores=bool(on)))
 
 
 def tune_batch(batch: Batch, ys, outs, fbs: Optional[Iterable[int]] = None,
@@ -125,9 +126,12 @@ def tune_batch(batch: Batch, ys, outs, fbs: Optional[Iterable[int]] = None,
     return dict(out, cached=False)
 
 
+_SHAPE_KEYS = ("frames_per_thread", "ctas_per_sm", "staging", "load_width", "tensor_cores")
+
+
 def _apply(plan: Plan, cfg: dict) -> None:
-    plan.set_tuning(cfg.get("frames_per_thread", 0), cfg.get("ctas_per_sm", 0), cfg.get("staging", False),
-                    cfg.get("load_width", 0), cfg.get("tensor_cores", False))
+    """The forward-kernel shape of `cfg`; the plan's other settings kept."""
+    plan.set_tuning(**dict(plan.tuning(), **{k: cfg.get(k, plan.tuning()[k]) for k in _SHAPE_KEYS}))
 
 
 def tune_plan(plan: Plan, y, out, fbs: Optional[Iterable[int]] = None, staging=(False, True),

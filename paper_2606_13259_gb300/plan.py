@@ -138,6 +138,16 @@ class Plan:
                      1 if tensor_cores else 0, int(tc_chain), int(voxels_per_thread), int(adjoint_rows),
                      int(host_io))
         L.check(self._lib.das_plan_set_tuning(self._h, C.byref(t)))
+        self._tuning = dict(frames_per_thread=int(frames_per_thread), ctas_per_sm=int(ctas_per_sm),
+                            staging=bool(staging), load_width=int(load_width), tensor_cores=bool(tensor_cores),
+                            tc_chain=int(tc_chain), voxels_per_thread=int(voxels_per_thread),
+                            adjoint_rows=int(adjoint_rows), host_io=int(host_io))
+
+    def tuning(self) -> dict:
+        """The tuning last set on this plan (all defaults before any set_tuning)."""
+        return dict(getattr(self, "_tuning", {}) or dict(
+            frames_per_thread=0, ctas_per_sm=0, staging=False, load_width=0, tensor_cores=False, tc_chain=0,
+            voxels_per_thread=0, adjoint_rows=0, host_io=0))
 
     def check(self, stream=None) -> None:
         """Wait for the stream; raise if a kernel recorded a failure (a bounded wait that expired)."""
