@@ -224,9 +224,10 @@ __global__ void __launch_bounds__(ADJ_THREADS, 2) adjoint_kernel(const AdjArgs A
                     float c0r, c0i = 0.f, c1r, c1i = 0.f;
                     if constexpr (IQ) {
                         float sn, cs;
-                        __sincosf(A.theta * (al - 0.5f), &sn, &cs);
-                        const float uhr = cs * A.hr - sn * A.hi, uhi = cs * A.hi + sn * A.hr;
-                        const float ubr = cs * A.hr + sn * A.hi, ubi = sn * A.hr - cs * A.hi;
+                        // e^{i th a} directly, e^{-i th (1-a)} = e^{i th a} e^{-i th}
+                        __sincosf(A.theta * al, &sn, &cs);
+                        const float uhr = cs, uhi = sn;
+                        const float ubr = cs * A.er - sn * A.ei, ubi = cs * A.ei + sn * A.er;
                         const float w0 = w * (1.f - al), w1 = w * al;
                         // conjugated coefficients of the two taps (pre-rotated sample domain)
                         c0r = w0 * uhr; c0i = -w0 * uhi; c1r = w1 * ubr; c1i = -w1 * ubi;

@@ -1090,6 +1090,8 @@ int das_adjoint(das_plan_t *plan, const void *x_dev, void *y_dev, int batch, das
     A.rows = rows;
     A.n_bands = n_bands;
     A.aRi = (int)ceil((double)A.a * (double)A.tile_radius) + 2;
+    A.er = (float)cos(2.0 * M_PI * plan->f_demod / plan->fs);
+    A.ei = (float)-sin(2.0 * M_PI * plan->f_demod / plan->fs);
     A.w_tx = plan->w_tx;
     A.rot = plan->rot;
     A.x = x_dev;

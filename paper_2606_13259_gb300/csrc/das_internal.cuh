@@ -116,6 +116,7 @@ struct AdjArgs {
     float a;
     float theta;
     float hr, hi;
+    float er, ei;          // e^{-i theta}
     float thr;
     float tile_radius;
     const double *elem_pos;
