@@ -29,6 +29,12 @@
 namespace das {
 
 constexpr int ADJ_THREADS = 512;  // 32 tiles x 16 voxel lines in flight per CTA
+// CTAs per SM asked of the compiler: two (64 registers, a few spilled words)
+// ran the differentiation workload's adjoint in 23.4 ms, one (96-114
+// registers, no spills, half the warps) in 36.4 ms.
+#ifndef ADJ_MINB
+#define ADJ_MINB 2
+#endif
 
 struct AdjTileRec {
     float gx, gy, gz, d0;  // tile centre minus element, and its norm
@@ -39,7 +45,7 @@ struct AdjTileRec {
 };
 
 template <bool IQ, int FB>
-__global__ void __launch_bounds__(ADJ_THREADS, 2) adjoint_kernel(const AdjArgs A) {
+__global__ void __launch_bounds__(ADJ_THREADS, ADJ_MINB) adjoint_kernel(const AdjArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int C = IQ ? 2 : 1;
     const int m = blockIdx.x;
