@@ -47,6 +47,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return done != 0;
 }
 
+// The same test with a suspend-time hint: a thread whose phase is not yet
+// complete sleeps until it completes or `hint_ns` ns have passed, instead of
+// returning after the hardware's own short limit.  A waiting thread then
+// issues a few instructions per hand-off instead of spinning, which leaves
+// the issue slots of its SM sub-partition to the warps doing the work.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, uint32_t parity, uint32_t hint_ns) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return done != 0;
+}
 
 __device__ __forceinline__ uint64_t global_ns() {
     uint64_t t;

@@ -52,15 +52,21 @@
 //   D: TMEM columns 0 .. n-1, lanes = voxels.
 //
 // CTA roles (G 128-thread builder groups + 2 warps): the builder threads
-// compute the work list and build W (thread = voxel = TMEM lane, group g
-// takes the sub-items with index = g mod G) and store D; lanes 0-3 of the
-// next warp issue the window copies; lane 0 of the last warp issues the MMAs
-// and their commits.  Stages are handed over with mbarriers: fullA (one
-// arrival per builder warp of a group), fullB (TMA transaction bytes),
-// emptyA / emptyB (tcgen05.commit of the MMAs that read the stage), accFull
-// (commit after the last MMA of a chain).  Every wait is bounded; on expiry
-// the CTA sets bit 2 of the plan's error word, drains what it has in flight
-// and leaves without writing its image tile.
+// compute the work list and build W (thread = voxel = TMEM lane) and store D;
+// lanes of the next warp issue the window copies; lane 0 of the last warp
+// issues the MMAs and their commits.  The roles hand sub-items over in
+// bundles of H (two where the tensor memory holds two bundles of W stages):
+// group g builds the bundles with index = g mod G.  Each hand-off of the
+// MMA-issuing thread (a barrier test, a commit) costs it about as much as an
+// MMA, and that thread's serial work, not the tensor core, bounds the kernel,
+// so a bundle takes one test of each full barrier and one commit for H
+// sub-items.  Barriers: fullA (one arrival per builder warp of the group),
+// fullB (TMA transaction bytes of the bundle's windows), empty
+// (tcgen05.commit of the bundle's MMAs: it frees the bundle's window slots
+// and W stages alike), accFull (commit after the last MMA of a chain).
+// Every wait is bounded; on expiry the CTA sets bit 2 of the plan's error
+// word, drains what it has in flight and leaves without writing its image
+// tile.
 #include "das_async.cuh"
 #include "das_tc.cuh"
 
@@ -76,7 +82,8 @@ namespace das {
 __host__ __device__ constexpr int tc_threads(int G) { return G * TILE_N + 64; }
 constexpr int TC_U = 16;        // window rows per sub-item
 constexpr int TC_KV = TC_U - 1; // values of k a sub-item covers
-constexpr int TC_MAX_SA = 16;   // W stages in TMEM (power of two, set per launch)
+constexpr int TC_MAX_SA = 16;   // W stages in TMEM (set per launch)
+
 constexpr int TC_ACOLS = 16;    // TMEM columns per W stage
 constexpr int TC_LIST_MAX = 4096;    // sub-items per list round (largest list)
 constexpr int TC_MAX_SB = 24;
@@ -179,6 +186,15 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
 }
 
 constexpr uint64_t TC_WAIT_NS = 1000000000ull;  // 1 s
+#ifndef TC_SLEEP_HINT_NS
+#define TC_SLEEP_HINT_NS 8192
+#endif
+constexpr uint32_t TC_SLEEP_NS = TC_SLEEP_HINT_NS;  // suspend-time hint of a waiting thread (0: none)
+
+// One test of a barrier phase with the suspend-time hint.
+__device__ __forceinline__ bool tc_try(uint64_t *bar, uint32_t parity) {
+    return TC_SLEEP_NS != 0 ? mbar_try_wait_sleep(bar, parity, TC_SLEEP_NS) : mbar_try_wait(bar, parity);
+}
 
 // Wait limit of the pipeline's hand-offs: the plan's test setting, else 1 s.
 __device__ __forceinline__ uint64_t tc_limit(const TcArgs &A) { return A.wait_ns ? A.wait_ns : TC_WAIT_NS; }
@@ -190,8 +206,8 @@ __device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity, volatile
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     for (uint32_t i = 1;; ++i) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((i & 63u) == 0u) {
+        if (tc_try(bar, parity)) return true;
+        if ((i & 7u) == 0u) {
             if (*abort_flag || (*(volatile int *)err & 4)) {
                 *abort_flag = 1u;
                 return false;
@@ -219,8 +235,8 @@ __device__ __noinline__ bool tc_wait_warp(uint64_t *bar, uint32_t parity, volati
                                           uint64_t limit) {
     const uint64_t t0 = global_ns();
     for (uint32_t i = 1;; ++i) {
-        if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
-        if ((i & 63u) == 0u) {
+        if (__all_sync(0xffffffffu, tc_try(bar, parity))) return true;
+        if ((i & 7u) == 0u) {
             const bool give_up = __any_sync(0xffffffffu, *abort_flag != 0u || (*(volatile int *)err & 4) != 0 ||
                                                              global_ns() - t0 > limit);
             if (give_up) break;
@@ -306,7 +322,7 @@ __device__ __noinline__ void tc_store_d(const TcArgs &A, uint32_t taddr, uint64_
     bool ok = true;
     if (read_d && lane == 0) {
         const uint64_t t0 = global_ns();
-        while (!(ok = mbar_try_wait(accFull, parity)))
+        while (!(ok = tc_try(accFull, parity)))
             if (global_ns() - t0 > TC_WAIT_NS) break;
         if (!ok) {
             atomicOr(A.err, 4);
@@ -347,7 +363,7 @@ __device__ __noinline__ void tc_store_d(const TcArgs &A, uint32_t taddr, uint64_
     tc_fence_before();
 }
 
-template <bool BF16, int G, int MINB, bool CHAIN>
+template <bool BF16, int G, int MINB, bool CHAIN, int HAND>
 __global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_constant__ CUtensorMap zmap,
                                                                  const __grid_constant__ TcArgs A) {
     constexpr int NB = G * TILE_N;  // builder threads
@@ -356,12 +372,17 @@ __global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_co
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
     const int Q = A.Q, M = A.M, K = A.K, n = A.n, sb = A.sb;
-    const uint32_t sa_n = (uint32_t)A.sa, sa_shift = (uint32_t)(31 - __clz(A.sa));
+    // sub-items per hand-off (a bundle), W bundle stages in tensor memory,
+    // window bundle slots in shared memory, producer lanes
+    constexpr uint32_t H = HAND;
+    const uint32_t pa_n = (uint32_t)A.sa / H;
+    const uint32_t pb_n = (uint32_t)A.sb / H, nprod = TC_PRODUCERS / H;
     const bool has_w = A.w_tx != nullptr;
     const TcSmem L = tc_smem_layout(sb, n, Q, has_w, EB, list_cap);
     const uint32_t stage_bytes = 64u * (uint32_t)n;
     unsigned char *sB = smem;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L.bars);
+    // fullB / emptyB: one per window bundle slot; fullA / emptyA: one per W bundle stage
     uint64_t *fullB = bars, *emptyB = bars + TC_MAX_SB, *fullA = bars + 2 * TC_MAX_SB, *emptyA = fullA + TC_MAX_SA;
     uint64_t *accFull = emptyA + TC_MAX_SA;
     uint64_t *probe = accFull + 1;  // test hook: a barrier nothing arrives on
@@ -391,12 +412,12 @@ __global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_co
     const int tz = (int)(tile / ((long long)g.tiles_x * g.tiles_y));
 
     if (tid == 0) {
-        for (int s = 0; s < sb; ++s) {
+        for (uint32_t s = 0; s < pb_n; ++s) {
             mbar_init(&fullB[s], 1);
             mbar_init(&emptyB[s], 1);
         }
-        for (int s = 0; s < A.sa; ++s) {
-            mbar_init(&fullA[s], TILE_N / 32);  // one arrival per builder warp of the item's group
+        for (uint32_t s = 0; s < pa_n; ++s) {
+            mbar_init(&fullA[s], TILE_N / 32);  // one arrival per builder warp of the bundle's group
             mbar_init(&emptyA[s], 1);
         }
         mbar_init(accFull, 1);
@@ -453,7 +474,13 @@ __global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_co
     uint32_t tma_issued = 0;  // producer: window copies issued
     // position in the window ring of this thread's role (producer, MMA
     // issuer): slot, completed passes over the ring (its low bit is the phase)
-    uint32_t b_slot = (warp == NB / 32 && lane < TC_PRODUCERS) ? (uint32_t)lane : 0u, b_pass = 0;
+    uint32_t b_slot = (warp == NB / 32 && (uint32_t)lane < nprod) ? (uint32_t)lane : 0u, b_pass = 0;
+    uint32_t bbase = 0;  // bundles of earlier rounds (same value in every thread)
+    // builders: W bundle stage of the group's next bundle (its bundles are grp,
+    // grp + G, ... across rounds) and the uses of that stage before it; MMA
+    // issuer: the same for its next bundle
+    uint32_t bps = (uint32_t)(tid >> 7) % pa_n, bpass = (uint32_t)(tid >> 7) / pa_n;
+    uint32_t mps = 0, mpass = 0;
 
     for (int m0 = 0; m0 < M; m0 += EB) {
         const int mend = min(M, m0 + EB);
@@ -600,11 +627,16 @@ __global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_co
                 bool inside = false;
                 float r = 0.f;
                 int Rb = 0;
-                bool pending = false;  // a stored stage whose completion is not yet signalled
-                uint32_t pend_sa = 0;
-                for (int e = (int)((grp + (uint32_t)G - base % (uint32_t)G) % (uint32_t)G); e < n_list && !stop;
-                     e += G) {
-                    const uint32_t gi = base + (uint32_t)e;  // global sub-item index
+                bool pending = false;  // a stored bundle whose completion is not yet signalled
+                uint32_t pend_ps = 0;
+                const int nb = (n_list + (int)H - 1) / (int)H;  // bundles of this round
+                for (int e2 = (int)((grp + (uint32_t)G - bbase % (uint32_t)G) % (uint32_t)G); e2 < nb && !stop;
+                     e2 += G) {
+                  const uint32_t gb = bbase + (uint32_t)e2;  // global bundle index
+                  const uint32_t ps = bps;
+                  const int e0 = e2 * (int)H, nh = min((int)H, n_list - e0);
+                  for (int h = 0; h < nh; ++h) {
+                    const int e = e0 + h;
                     const int2 ent = s_list[e];
                     const int j = ent.y & 511, q = (ent.y >> 9) & 127;
                     if (j != last_j) {
@@ -654,48 +686,60 @@ __global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_co
                         v[c] = __byte_perm(pr, 0u, sw[c]);
                         v[8 + c] = __byte_perm(pi, 0u, sw[c]);
                     }
-                    // the group's previous store has drained while v was built: signal it
-                    tmem_st_wait();
-                    tc_fence_before();
-                    __syncwarp();
-                    mbar_arrive_if(&fullA[pend_sa], pending && lane == 0);
-                    const uint32_t sa = gi & (sa_n - 1u), use = gi >> sa_shift;
-                    const bool ready = __all_sync(0xffffffffu, use == 0 || mbar_try_wait(&emptyA[sa], (use - 1) & 1u));
-                    if (!ready && !tc_wait_warp(&emptyA[sa], (use - 1) & 1u, s_abort, A.err, tc_limit(A))) {
+                    if (h == 0) {
+                        // the group's previous bundle has drained while v was built: signal it
+                        tmem_st_wait();
+                        tc_fence_before();
+                        __syncwarp();
+                        mbar_arrive_if(&fullA[pend_ps], pending && lane == 0);
                         pending = false;
-                        stop = true;
-                        break;
+                        // this bundle's W stages are free once the MMAs of their previous use completed
+                        if (bpass > 0) {
+                            const uint32_t par = (bpass - 1u) & 1u;
+                            const bool ready = __all_sync(0xffffffffu, mbar_try_wait(&emptyA[ps], par));
+                            if (!ready && !tc_wait_warp(&emptyA[ps], par, s_abort, A.err, tc_limit(A))) {
+                                stop = true;
+                                break;
+                            }
+                        }
+                        tc_fence_after();
                     }
-                    tc_fence_after();
-                    tmem_st16(tmem + lane_base + (uint32_t)n + TC_ACOLS * sa, v);
-                    pending = true;
-                    pend_sa = sa;
+                    tmem_st16(tmem + lane_base + (uint32_t)n + TC_ACOLS * (ps * H + (uint32_t)h), v);
+                  }
+                  if (stop) break;
+                  pending = true;
+                  pend_ps = ps;
+                  for (bps += G; bps >= pa_n; ++bpass) bps -= pa_n;
                 }
                 tmem_st_wait();
                 tc_fence_before();
                 __syncwarp();
-                mbar_arrive_if(&fullA[pend_sa], pending && lane == 0);
+                mbar_arrive_if(&fullA[pend_ps], pending && lane == 0);
             } else if (warp == NB / 32) {
-                // ---- producer: window copies, TC_PRODUCERS lanes; lane L takes the
-                // sub-items with global index = L mod TC_PRODUCERS, whose ring slots
-                // are = L mod TC_PRODUCERS (the stage count is a multiple of it) ----
-                if (lane < TC_PRODUCERS) {
-                    for (int e = (int)(((uint32_t)lane + TC_PRODUCERS - base % TC_PRODUCERS) % TC_PRODUCERS);
-                         e < n_list && !stop; e += TC_PRODUCERS) {
-                        const uint32_t gi = base + (uint32_t)e;
-                        const int2 ent = s_list[e];
-                        const int j = ent.y & 511, q = (ent.y >> 9) & 127;
+                // ---- producer: window copies, nprod lanes; lane L takes the bundles
+                // with global index = L mod nprod, whose ring slots are = L mod nprod
+                // (the slot count is a multiple of it); one barrier per bundle ----
+                if ((uint32_t)lane < nprod) {
+                    const int nb = (n_list + (int)H - 1) / (int)H;
+                    for (int e2 = (int)(((uint32_t)lane + nprod - bbase % nprod) % nprod); e2 < nb && !stop;
+                         e2 += (int)nprod) {
+                        const uint32_t gb = bbase + (uint32_t)e2;
                         if (b_pass > 0 && !tc_wait(&emptyB[b_slot], (b_pass - 1) & 1u, s_abort, A.err, tc_limit(A))) {
                             stop = true;
                             break;
                         }
-                        mbar_arrive_expect_tx(&fullB[b_slot], stage_bytes);
-                        tma_load_4d(sB + (size_t)b_slot * stage_bytes, &zmap, 8 * ent.x, 0, 0,
-                                    (int)(qm_base + (size_t)q * M + s_em[j]), &fullB[b_slot]);
-                        tma_issued = gi + 1u;
-                        b_slot += TC_PRODUCERS;
-                        if (b_slot >= (uint32_t)sb) {
-                            b_slot -= (uint32_t)sb;
+                        const int e0 = e2 * (int)H, nh = min((int)H, n_list - e0);
+                        mbar_arrive_expect_tx(&fullB[b_slot], stage_bytes * (uint32_t)nh);
+                        for (int h = 0; h < nh; ++h) {
+                            const int2 ent = s_list[e0 + h];
+                            const int j = ent.y & 511, q = (ent.y >> 9) & 127;
+                            tma_load_4d(sB + (size_t)(b_slot * H + (uint32_t)h) * stage_bytes, &zmap, 8 * ent.x, 0, 0,
+                                        (int)(qm_base + (size_t)q * M + s_em[j]), &fullB[b_slot]);
+                        }
+                        tma_issued = gb + 1u;
+                        b_slot += nprod;
+                        if (b_slot >= pb_n) {
+                            b_slot -= pb_n;
                             ++b_pass;
                         }
                     }
@@ -711,32 +755,43 @@ __global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_co
                     if (A.probe && blockIdx.x == 0 && blockIdx.y == 0 && base == 0 && n_list > 0 &&
                         !tc_wait(probe, 0u, s_abort, A.err, tc_limit(A)))
                         stop = true;
-                    for (int e = 0; e < n_list && !stop; ++e) {
-                        const uint32_t gi = base + (uint32_t)e;
-                        const uint32_t sa = gi & (sa_n - 1u), slot = b_slot;
-                        if (!tc_wait(&fullA[sa], (gi >> sa_shift) & 1u, s_abort, A.err, tc_limit(A)) ||
+                    const int nb = (n_list + (int)H - 1) / (int)H;
+                    for (int e2 = 0; e2 < nb && !stop; ++e2) {
+                        const uint32_t gb = bbase + (uint32_t)e2;  // global bundle index
+                        const uint32_t ps = mps, slot = b_slot;
+                        if (!tc_wait(&fullA[ps], mpass & 1u, s_abort, A.err, tc_limit(A)) ||
                             !tc_wait(&fullB[slot], b_pass & 1u, s_abort, A.err, tc_limit(A))) {
                             stop = true;
                             break;
                         }
-                        if (++b_slot == (uint32_t)sb) {
+                        if (++mps == pa_n) {
+                            mps = 0;
+                            ++mpass;
+                        }
+                        if (++b_slot == pb_n) {
                             b_slot = 0;
                             ++b_pass;
                         }
                         tc_fence_after();
-                        const uint32_t a_col = tmem + (uint32_t)n + TC_ACOLS * sa;
-                        const uint64_t bdesc = bdesc0 + (uint64_t)((slot * stage_bytes) >> 4);
-                        // the first sub-item of a chain starts from zero
-                        mma_ts(tmem, a_col, bdesc, idesc, (CHAIN ? gi != chain0 : gi > 0) ? 1u : 0u);
-                        mma_ts(tmem, a_col + 8, bdesc + (256 >> 4), idesc, 1u);
-                        mma_commit(&emptyA[sa]);
+                        const int e0 = e2 * (int)H, nh = min((int)H, n_list - e0);
+                        for (int h = 0; h < nh; ++h) {
+                            const uint32_t gi = base + (uint32_t)(e0 + h);  // global sub-item index
+                            const uint32_t a_col = tmem + (uint32_t)n + TC_ACOLS * (ps * H + (uint32_t)h);
+                            const uint64_t bdesc = bdesc0 + (uint64_t)(((slot * H + (uint32_t)h) * stage_bytes) >> 4);
+                            // the first sub-item of a chain starts from zero
+                            mma_ts(tmem, a_col, bdesc, idesc, (CHAIN ? gi != chain0 : gi > 0) ? 1u : 0u);
+                            mma_ts(tmem, a_col + 8, bdesc + (256 >> 4), idesc, 1u);
+                        }
+                        // the bundle's W stages and window slots are free once these MMAs complete
+                        mma_commit(&emptyA[ps]);
                         mma_commit(&emptyB[slot]);
-                        done = gi + 1u;
+                        done = base + (uint32_t)(e0 + nh);
                     }
                     if (done) misc[MW_ISSUED] = done;
                 }
             }
             base += (uint32_t)n_list;
+            bbase += (uint32_t)((n_list + (int)H - 1) / (int)H);
             p0 = p_next;
             __syncthreads();  // list and element records of this round no longer read
             stop = stop || *s_abort != 0u;
@@ -762,7 +817,7 @@ __global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_co
             bool ok = true;
             if (issued > 0 && lane == 0) {
                 const uint64_t t0 = global_ns();
-                while (!(ok = mbar_try_wait(accFull, 0u)))
+                while (!(ok = tc_try(accFull, 0u)))
                     if (global_ns() - t0 > TC_WAIT_NS) break;
                 if (!ok) atomicOr(A.err, 4);
             }
@@ -793,16 +848,16 @@ __global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_co
             }
             tc_fence_before();
         }
-    } else if (warp == NB / 32 && lane < TC_PRODUCERS && *s_abort != 0u && tma_issued > 0) {
+    } else if (warp == NB / 32 && (uint32_t)lane < nprod && *s_abort != 0u && tma_issued > 0) {
         // copies this lane still has in flight land before the CTA leaves:
-        // wait for its last uses of the ring (bounded by time)
+        // wait for its last bundles of the ring (bounded by time)
         const uint64_t t0 = global_ns();
         uint32_t i = tma_issued - 1u;
-        for (int c = 0; c < sb / TC_PRODUCERS; ++c) {
-            while (!mbar_try_wait(&fullB[i % (uint32_t)sb], (i / (uint32_t)sb) & 1u))
+        for (uint32_t c = 0; c < pb_n / nprod; ++c) {
+            while (!tc_try(&fullB[i % pb_n], (i / pb_n) & 1u))
                 if (global_ns() - t0 > TC_WAIT_NS) break;
-            if (i < (uint32_t)TC_PRODUCERS) break;
-            i -= TC_PRODUCERS;
+            if (i < nprod) break;
+            i -= nprod;
         }
     }
     __syncthreads();
@@ -924,7 +979,8 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 
 template <bool BF16, int G, int MINB>
 static cudaError_t launch_tc_t(const CUtensorMap &map, const TcArgs &A, size_t smem, int nch, cudaStream_t s) {
-    auto kern = A.chain > 0 ? tc_kernel<BF16, G, MINB, true> : tc_kernel<BF16, G, MINB, false>;
+    auto kern = A.chain > 0 ? (A.hand == 2 ? tc_kernel<BF16, G, MINB, true, 2> : tc_kernel<BF16, G, MINB, true, 1>)
+                            : (A.hand == 2 ? tc_kernel<BF16, G, MINB, false, 2> : tc_kernel<BF16, G, MINB, false, 1>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)n_tiles(A.g), (unsigned)nch);
@@ -942,8 +998,8 @@ cudaError_t launch_tc(const TcArgs &args, int bf16, const void *z, int nch, int 
     // accumulator and two W stages fit 128 tensor-memory columns (N <= 96, up
     // to 48 frames) and the CTA's tables and window stages fit a quarter of the
     // shared memory, so that four MMA-issuing threads per SM overlap their
-    // per-sub-item hand-offs (paper workload, 20 frames: 119.3 ms against
-    // 166.7 ms with two CTAs); else two while they fit half of the tensor
+    // per-sub-item hand-offs (paper workload, 20 frames: 112.5 ms against
+    // 137.3 ms with two CTAs); else two while they fit half of the tensor
     // memory and of the shared memory, else one.  Three, or the others, on
     // request (refused when they do not fit).
     const bool has_w = A.w_tx != nullptr;
@@ -953,8 +1009,9 @@ cudaError_t launch_tc(const TcArgs &args, int bf16, const void *z, int nch, int 
         if (ps >= 3 && A.n + 2 * TC_ACOLS > 128) return false;
         if (ps == 2 && A.n + 2 * TC_ACOLS > 256) return false;
         A.ncols = ps >= 3 ? 128 : 512 / ps;
-        int sa = 1;
-        while (2 * sa <= TC_MAX_SA && A.n + 2 * sa * TC_ACOLS <= A.ncols) sa *= 2;
+        // W stages: as many as the columns left beside the accumulator hold
+        int sa = (A.ncols - A.n) / TC_ACOLS;
+        if (sa > TC_MAX_SA) sa = TC_MAX_SA;
         if (sa < 2) return false;
         A.sa = sa;
         G = ps >= 3 ? 1 : ps == 2 ? 2 : 4;
@@ -972,7 +1029,16 @@ cudaError_t launch_tc(const TcArgs &args, int bf16, const void *z, int nch, int 
         sbv = fixed < budget ? (int)((budget - fixed) / stage) : 0;
         if (sbv > TC_MAX_SB) sbv = TC_MAX_SB;
         sbv -= sbv % TC_PRODUCERS;
-        return sbv >= TC_PRODUCERS;
+        if (sbv < TC_PRODUCERS) return false;
+        // sub-items per hand-off: two while the W ring holds two bundles and at
+        // least G (a group's wait on a stage is then at most one phase ahead of
+        // it); paper workload, 20 frames, four CTAs per SM: 112.5 ms against
+        // 118.1 ms with single sub-items
+        int H = sa / 2 >= 2 && sa / 2 >= G ? 2 : 1;
+        if (sa / H < G) return false;
+        A.hand = H;
+        A.sa = (sa / H) * H;
+        return true;
     };
     int per_sm = 0;
     if (ctas_per_sm > 0) {

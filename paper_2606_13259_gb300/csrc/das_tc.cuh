@@ -20,7 +20,8 @@ struct TcArgs {
     int bc;           // frames per chunk: MMA columns 0..bc-1 carry real parts, bc..2bc-1 imaginary parts
     int n;            // MMA N: 2 bc rounded up to a multiple of 16 (<= 256)
     int sb;           // window stages in shared memory
-    int sa;           // weight stages in tensor memory (power of two)
+    int sa;           // weight stages in tensor memory (a multiple of hand)
+    int hand;         // sub-items per hand-off between the roles (1 or 2; divides sa and sb)
     int list_cap;     // sub-items per work list
     int chain;        // sub-items per accumulation chain before D is added into x (0: one chain)
     int ncols;        // tensor-memory columns the CTA allocates
