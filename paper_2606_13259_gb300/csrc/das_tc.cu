@@ -620,7 +620,7 @@ __global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_co
             const int p_next = (int)misc[MW_NEXT];
 
             if (tid < NB) {
-                // ---- builders: group `grp` writes the W rows of the sub-items with index = grp mod G ----
+                // ---- builders: group `grp` writes the W rows of the bundles with index = grp mod G ----
                 const uint32_t grp = (uint32_t)(tid >> 7);
                 const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
                 int last_j = -1;
@@ -632,84 +632,83 @@ __global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_co
                 const int nb = (n_list + (int)H - 1) / (int)H;  // bundles of this round
                 for (int e2 = (int)((grp + (uint32_t)G - bbase % (uint32_t)G) % (uint32_t)G); e2 < nb && !stop;
                      e2 += G) {
-                  const uint32_t gb = bbase + (uint32_t)e2;  // global bundle index
-                  const uint32_t ps = bps;
-                  const int e0 = e2 * (int)H, nh = min((int)H, n_list - e0);
-                  for (int h = 0; h < nh; ++h) {
-                    const int e = e0 + h;
-                    const int2 ent = s_list[e];
-                    const int j = ent.y & 511, q = (ent.y >> 9) & 127;
-                    if (j != last_j) {
-                        last_j = j;
-                        const float4 G4 = s_eg[j];
-                        const float4 Nn = s_en[j];
-                        Rb = s_erb[j];
-                        const float ex = G4.x + dx, ey = G4.y + dy, ez = G4.z + dz;
-                        inside = valid;
-                        if (A.thr >= 0.f) {
-                            const float zax = fmaf(ex, Nn.x, fmaf(ey, Nn.y, ez * Nn.z));
-                            const float cx = fmaf(ey, Nn.z, -ez * Nn.y), cy = fmaf(ez, Nn.x, -ex * Nn.z),
-                                        cz = fmaf(ex, Nn.y, -ey * Nn.x);
-                            const float rho2 = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
-                            inside = inside && (zax > 0.f) && (rho2 <= A.thr * zax * zax);
-                        }
-                        const float d = sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
-                        const float num = fmaf(2.f, fmaf(G4.x, dx, fmaf(G4.y, dy, G4.z * dz)), dd);
-                        r = Nn.w + A.a * __fdividef(num, d + G4.w);
-                    }
-                    const float f = r + s_t[q * TILE_N + vl];
-                    const float fl = floorf(f);
-                    const float al = f - fl;
-                    const int k = s_tb[q] + Rb + (int)fl;
-                    const bool act = inside && (unsigned)k <= (unsigned)(K - 2);
-                    const int u = k - ent.x;
-                    float w = has_w ? s_w[q * TILE_N + vl] : 1.f;
-                    w *= s_lw[e];
-                    // e^{i th a} directly (th a in [0, th]; the weights are rounded to
-                    // 16 bits), and e^{-i th (1-a)} = e^{i th a} e^{-i th}
-                    float sn, cs;
-                    __sincosf(A.theta * al, &sn, &cs);
-                    const float uhr = cs, uhi = sn;
-                    const float ubr = cs * A.er - sn * A.ei, ubi = cs * A.ei + sn * A.er;
-                    const float w0 = w * (1.f - al), w1 = w * al;
-                    const uint32_t pr = pack2<BF16>(w0 * uhr, w1 * ubr);  // (Wr[u], Wr[u+1])
-                    const uint32_t pi = pack2<BF16>(w0 * uhi, w1 * ubi);  // (Wi[u], Wi[u+1])
-                    // the row: (value u, value u + 1) of each plane at 16-bit position u,
-                    // zeros elsewhere, by byte permutes with the selectors of row u
-                    const bool in = act && (unsigned)u < (unsigned)TC_KV;
-                    const uint4 *sel = reinterpret_cast<const uint4 *>(s_sel + 8 * (in ? u : TC_KV));
-                    const uint4 s0 = sel[0], s1 = sel[1];
-                    const uint32_t sw[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
-                    uint32_t v[16];
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        v[c] = __byte_perm(pr, 0u, sw[c]);
-                        v[8 + c] = __byte_perm(pi, 0u, sw[c]);
-                    }
-                    if (h == 0) {
-                        // the group's previous bundle has drained while v was built: signal it
-                        tmem_st_wait();
-                        tc_fence_before();
-                        __syncwarp();
-                        mbar_arrive_if(&fullA[pend_ps], pending && lane == 0);
-                        pending = false;
-                        // this bundle's W stages are free once the MMAs of their previous use completed
-                        if (bpass > 0) {
-                            const uint32_t par = (bpass - 1u) & 1u;
-                            const bool ready = __all_sync(0xffffffffu, mbar_try_wait(&emptyA[ps], par));
-                            if (!ready && !tc_wait_warp(&emptyA[ps], par, s_abort, A.err, tc_limit(A))) {
-                                stop = true;
-                                break;
+                    const uint32_t ps = bps;  // W bundle stage of this bundle
+                    const int e0 = e2 * (int)H, nh = min((int)H, n_list - e0);
+                    for (int h = 0; h < nh; ++h) {
+                        const int e = e0 + h;
+                        const int2 ent = s_list[e];
+                        const int j = ent.y & 511, q = (ent.y >> 9) & 127;
+                        if (j != last_j) {
+                            last_j = j;
+                            const float4 G4 = s_eg[j];
+                            const float4 Nn = s_en[j];
+                            Rb = s_erb[j];
+                            const float ex = G4.x + dx, ey = G4.y + dy, ez = G4.z + dz;
+                            inside = valid;
+                            if (A.thr >= 0.f) {
+                                const float zax = fmaf(ex, Nn.x, fmaf(ey, Nn.y, ez * Nn.z));
+                                const float cx = fmaf(ey, Nn.z, -ez * Nn.y), cy = fmaf(ez, Nn.x, -ex * Nn.z),
+                                            cz = fmaf(ex, Nn.y, -ey * Nn.x);
+                                const float rho2 = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
+                                inside = inside && (zax > 0.f) && (rho2 <= A.thr * zax * zax);
                             }
+                            const float d = sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
+                            const float num = fmaf(2.f, fmaf(G4.x, dx, fmaf(G4.y, dy, G4.z * dz)), dd);
+                            r = Nn.w + A.a * __fdividef(num, d + G4.w);
                         }
-                        tc_fence_after();
+                        const float f = r + s_t[q * TILE_N + vl];
+                        const float fl = floorf(f);
+                        const float al = f - fl;
+                        const int k = s_tb[q] + Rb + (int)fl;
+                        const bool act = inside && (unsigned)k <= (unsigned)(K - 2);
+                        const int u = k - ent.x;
+                        float w = has_w ? s_w[q * TILE_N + vl] : 1.f;
+                        w *= s_lw[e];
+                        // e^{i th a} directly (th a in [0, th]; the weights are rounded to
+                        // 16 bits), and e^{-i th (1-a)} = e^{i th a} e^{-i th}
+                        float sn, cs;
+                        __sincosf(A.theta * al, &sn, &cs);
+                        const float uhr = cs, uhi = sn;
+                        const float ubr = cs * A.er - sn * A.ei, ubi = cs * A.ei + sn * A.er;
+                        const float w0 = w * (1.f - al), w1 = w * al;
+                        const uint32_t pr = pack2<BF16>(w0 * uhr, w1 * ubr);  // (Wr[u], Wr[u+1])
+                        const uint32_t pi = pack2<BF16>(w0 * uhi, w1 * ubi);  // (Wi[u], Wi[u+1])
+                        // the row: (value u, value u + 1) of each plane at 16-bit position u,
+                        // zeros elsewhere, by byte permutes with the selectors of row u
+                        const bool in = act && (unsigned)u < (unsigned)TC_KV;
+                        const uint4 *sel = reinterpret_cast<const uint4 *>(s_sel + 8 * (in ? u : TC_KV));
+                        const uint4 s0 = sel[0], s1 = sel[1];
+                        const uint32_t sw[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
+                        uint32_t v[16];
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) {
+                            v[c] = __byte_perm(pr, 0u, sw[c]);
+                            v[8 + c] = __byte_perm(pi, 0u, sw[c]);
+                        }
+                        if (h == 0) {
+                            // the group's previous bundle has drained while v was built: signal it
+                            tmem_st_wait();
+                            tc_fence_before();
+                            __syncwarp();
+                            mbar_arrive_if(&fullA[pend_ps], pending && lane == 0);
+                            pending = false;
+                            // this bundle's W stages are free once the MMAs of their previous use completed
+                            if (bpass > 0) {
+                                const uint32_t par = (bpass - 1u) & 1u;
+                                const bool ready = __all_sync(0xffffffffu, mbar_try_wait(&emptyA[ps], par));
+                                if (!ready && !tc_wait_warp(&emptyA[ps], par, s_abort, A.err, tc_limit(A))) {
+                                    stop = true;
+                                    break;
+                                }
+                            }
+                            tc_fence_after();
+                        }
+                        tmem_st16(tmem + lane_base + (uint32_t)n + TC_ACOLS * (ps * H + (uint32_t)h), v);
                     }
-                    tmem_st16(tmem + lane_base + (uint32_t)n + TC_ACOLS * (ps * H + (uint32_t)h), v);
-                  }
-                  if (stop) break;
-                  pending = true;
-                  pend_ps = ps;
-                  for (bps += G; bps >= pa_n; ++bpass) bps -= pa_n;
+                    if (stop) break;
+                    pending = true;
+                    pend_ps = ps;
+                    for (bps += G; bps >= pa_n; ++bpass) bps -= pa_n;
                 }
                 tmem_st_wait();
                 tc_fence_before();
@@ -757,8 +756,7 @@ __global__ void __launch_bounds__(tc_threads(G), MINB) tc_kernel(const __grid_co
                         stop = true;
                     const int nb = (n_list + (int)H - 1) / (int)H;
                     for (int e2 = 0; e2 < nb && !stop; ++e2) {
-                        const uint32_t gb = bbase + (uint32_t)e2;  // global bundle index
-                        const uint32_t ps = mps, slot = b_slot;
+                        const uint32_t ps = mps, slot = b_slot;  // W bundle stage and window bundle slot
                         if (!tc_wait(&fullA[ps], mpass & 1u, s_abort, A.err, tc_limit(A)) ||
                             !tc_wait(&fullB[slot], b_pass & 1u, s_abort, A.err, tc_limit(A))) {
                             stop = true;
